@@ -1,0 +1,70 @@
+"""The pins must fail on a plausible mistake.  Each case plants one mistake in a
+copy of an oracle function (on the CPU) and checks that the corresponding pin
+detects it: a dropped penalty term in the Hessian, a wrong sign on the
+curvature term, a transposed operand in the gradient, a missing factor 2 in b."""
+import numpy as np
+
+from oracle import moment, operators as ops, subproblem as sp
+from tests.test_oracle_subproblem import setup, tangent
+
+
+def fd_hess_error(hess_fn):
+    prob, Xt, Y, rng = setup(seed=7)
+    sigma = 0.9
+    U = tangent(rng, Y)
+    H = hess_fn(Y, U, prob, Xt, sigma)
+    t = 1e-5
+    gp = sp.rgrad(sp.retract(Y, t * U), prob, Xt, sigma)
+    gm = sp.rgrad(sp.retract(Y, -t * U), prob, Xt, sigma)
+    fd = sp.proj_tangent(Y, (gp - gm) / (2 * t))
+    return np.abs(fd - H).max() / np.abs(H).max()
+
+
+def test_correct_hessian_passes():
+    assert fd_hess_error(sp.rhess) < 1e-6
+
+
+def test_dropped_penalty_term_caught():
+    def bad(Y, U, prob, Xt, sigma):
+        G = sp.egrad_S(Y, prob, Xt, sigma)
+        U = sp.proj_tangent(Y, U)
+        H = 2.0 * G @ U
+        z = sp.rowdot(G @ Y, Y)
+        return H - sp.rowdot(H, Y)[:, None] * Y - 2.0 * z[:, None] * U
+    assert fd_hess_error(bad) > 1e-3
+
+
+def test_wrong_curvature_sign_caught():
+    def bad(Y, U, prob, Xt, sigma):
+        G = sp.egrad_S(Y, prob, Xt, sigma)
+        U = sp.proj_tangent(Y, U)
+        H = sp.ehess(Y, U, prob, Xt, sigma, G)
+        z = sp.rowdot(G @ Y, Y)
+        return H - sp.rowdot(H, Y)[:, None] * Y + 2.0 * z[:, None] * U
+    assert fd_hess_error(bad) > 1e-3
+
+
+def test_transposed_gradient_operand_caught():
+    prob, Xt, Y, rng = setup(seed=8)
+    G = sp.egrad_S(Y, prob, Xt, 1.0)
+    G_bad = G + np.triu(np.ones_like(G), 1) * 0.1  # loses symmetry, as a mixed-up operand would
+    g_ok = sp.rgrad(Y, prob, Xt, 1.0)
+    g_bad = sp.proj_tangent(Y, 2.0 * G_bad.T @ Y)
+    U = tangent(rng, Y)
+    f = lambda t: sp.cost(sp.retract(Y, t * U), prob, Xt, 1.0)
+    fd = (f(1e-4) - f(-1e-4)) / 2e-4
+    assert abs(fd - np.sum(g_ok * U)) < 1e-6 * abs(fd)
+    assert abs(fd - np.sum(g_bad * U)) > 1e-3 * abs(fd)
+
+
+def test_missing_factor_two_in_rhs_caught():
+    q = 5
+    rng = np.random.default_rng(0)
+    Q = rng.standard_normal((q, q)); Q = Q + Q.T
+    c = rng.standard_normal(q)
+    b = moment.rhs(q, Q, c).copy()
+    b[1 + q:1 + q + q * (q - 1) // 2] *= 0.5
+    monos = moment.monomials(q)
+    x = np.array([1.0, -1.0, 1.0, 1.0, -1.0])
+    mv = np.array([np.prod(x[list(s)]) for s in monos])
+    assert abs(b @ mv - moment.bqp_objective(x, Q, c)) > 1e-3
