@@ -1,0 +1,212 @@
+/*
+ * manidsdp.h - C ABI of the GB300 ManiDSDP hot path.
+ *
+ * ManiDSDP (arXiv 2512.04406) solves the dual unit-diagonal SDP
+ *     inf_y b'y   s.t.  S = A*(y) - C >= 0,  diag(S) = 1          (DSDP)
+ * by the variable projection y(S) = (AA*)^{-1} A(S + C) (Section 3), an
+ * augmented Lagrangian on S (Algorithm 0), and a Burer-Monteiro factor
+ * S = Y Y' on the oblique manifold N_p = {Y in R^{N x p}: unit rows}
+ * (Section 4) whose subproblems are solved by Riemannian trust region
+ * (Algorithm 1).
+ *
+ * Scope of this library: constraint operators A whose coefficient matrices are
+ * 0/1 indicators of disjoint entry sets ("index maps"), as in moment
+ * relaxations of binary and unit-modulus problems.  Then A A* is the diagonal
+ * of multiplicities (remark on A A* after Algorithm 1), y(S) is a per-class
+ * mean of S + C, and A*(y) scatters the means back.
+ *
+ * Conventions
+ *   - All matrices are row-major.  Y, U, HU are N x p with leading dimension p.
+ *   - "host or device" pointers are copied with cudaMemcpyDefault (unified
+ *     addressing); "device" pointers must be device memory of the context's
+ *     device.  The library never frees caller memory; callers never free
+ *     library memory except through manidsdp_destroy.
+ *   - Every entry point enqueues its work on the stream given to
+ *     manidsdp_setup and returns only after the results it reports to the
+ *     host are complete (entry points that write device outputs synchronise
+ *     the stream before returning as well).
+ *   - Return value: MANIDSDP_OK (0) or a negative status.  On
+ *     MANIDSDP_E_ARG nothing is written.  No C++ exception crosses the ABI.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MANIDSDP_H
+#define MANIDSDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MANIDSDP_OK 0
+#define MANIDSDP_E_ARG (-1)       /* bad shape/pointer, idx out of [0,m), idx not
+                                     symmetric, or a class with no entry (then
+                                     A A* is singular: Assumption 2 fails) */
+#define MANIDSDP_E_NONFINITE (-2) /* NaN/Inf met in inputs or iterates */
+#define MANIDSDP_E_NOCONV (-3)    /* iteration limit reached; outputs hold the
+                                     last iterate */
+#define MANIDSDP_E_TIMEOUT (-4)   /* a device-side wait hit its iteration cap */
+#define MANIDSDP_E_CUDA (-5)      /* a CUDA runtime call failed */
+#define MANIDSDP_E_NOMEM (-6)     /* device allocation failed */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define MANIDSDP_C_ZERO 0  /* C = 0 (BQP moment relaxations, Section 6.1) */
+#define MANIDSDP_C_DENSE 1 /* C given as a dense symmetric N x N FP64 matrix */
+
+#define MANIDSDP_PREC_FP64 0  /* every step in FP64 */
+#define MANIDSDP_PREC_MIXED 1 /* Hessian-vector products (tCG) in FP32 with FP32
+                                 accumulation; cost, gradient, multiplier update,
+                                 KKT residuals and Lanczos in FP64 */
+
+#define MANIDSDP_EIG_MIN 0
+#define MANIDSDP_EIG_MAX 1
+
+typedef struct manidsdp_ctx manidsdp_ctx; /* opaque, owned by the library */
+
+/* Algorithm 1 inputs (sigma_0, sigma_min, sigma_max, gamma, kappa_1, kappa_2,
+ * p_0) and the knobs of the readings the paper leaves open: inner tolerance
+ * eps_k = clamp(tol_grad_factor * ||R^k|| / (1 + ||b||), tol_grad_min,
+ * tol_grad_max); rank drop below rank_tol * lambda_max(Y'Y) with p >= p_min;
+ * rank growth by at most delta_max eigenvectors whose eigenvalue is below
+ * -neg_tol * (1 + |lambda_max(X)|); tCG relative-residual floor tcg_floor;
+ * carried-direction line search with carry_halvings halvings from sqrt(N). */
+typedef struct {
+  double sigma0, sigma_min, sigma_max, gamma, kappa1, kappa2;
+  double tol;             /* stop when eta_max <= tol (Section 6) */
+  double tol_grad_min, tol_grad_max, tol_grad_factor;
+  double rank_tol, neg_tol, tcg_floor;
+  int32_t p0, p_min, p_max, delta_max;
+  int32_t max_outer, max_rtr, max_tcg, carry_halvings;
+  int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */
+  int32_t precision_mode; /* MANIDSDP_PREC_* */
+  int32_t verbose;        /* 1: one line per outer iteration on stderr */
+  int32_t reserved;
+} manidsdp_params;
+
+/* Per-solve report (host struct filled by manidsdp_solve). */
+typedef struct {
+  double eta_p, eta_d, eta_g; /* KKT residuals of Section 6 */
+  double value;               /* b'y: the relaxation value (dual objective) */
+  double pobj;                /* <C, X + Diag z> + sum(z) */
+  double lambda_min, lambda_max, sigma;
+  int32_t outer, rtr_iters, hessvecs, p;
+  int32_t lanczos_matvecs, status, reserved0, reserved1;
+} manidsdp_report;
+
+/* Fill *params with the library defaults (the readings listed above). */
+void manidsdp_default_params(manidsdp_params* params);
+
+/* Human-readable text for a status code (static storage). */
+const char* manidsdp_strerror(int status);
+
+/*
+ * manidsdp_setup - build a context for one SDP instance.
+ *   N       order of S (moment-matrix order), N >= 1.
+ *   m       number of constraint classes (monomials), m >= 1.
+ *   idx     host N x N int32: idx[b*N + g] = class of entry (b, g); must be
+ *           symmetric and cover every class in [0, m) at least once.  Copied.
+ *   b       host or device, m FP64: right-hand side.  Copied.
+ *   c_kind  MANIDSDP_C_ZERO or MANIDSDP_C_DENSE.
+ *   c_dense host or device N x N FP64 (symmetric) when c_kind is DENSE, else NULL.
+ *   params  NULL for defaults.  Copied.
+ *   stream  cudaStream_t cast to void* (NULL = legacy default stream).
+ * The context owns device copies of idx, its per-class inverse map (entries
+ * (b <= g) grouped by class in row-major order, split into pieces of at most
+ * 32 entries), 1/mult, b/mult (the values of D = A*(AA*)^{-1} b), the
+ * multiplier Xt (N x N FP64, zero) and all workspace.
+ * Definitions: Section 2 (A, A*), Section 3 (y(S), D), remark on AA*.
+ */
+int manidsdp_setup(manidsdp_ctx** ctx, int32_t N, int64_t m, const int32_t* idx,
+                   const double* b, int32_t c_kind, const double* c_dense,
+                   const manidsdp_params* params, void* stream);
+
+/* Release every resource of the context (NULL is a no-op). */
+void manidsdp_destroy(manidsdp_ctx* ctx);
+
+/* Replace the ALM state: multiplier Xt (host or device N x N FP64, NULL = zero)
+ * and penalty sigma.  Section 3, Algorithm 0. */
+int manidsdp_set_state(manidsdp_ctx* ctx, const double* Xt, double sigma);
+
+/* Copy out the multiplier Xt (host or device N x N FP64). */
+int manidsdp_get_multiplier(manidsdp_ctx* ctx, double* Xt);
+
+/*
+ * manidsdp_subproblem_eval - value and Riemannian gradient of the ALM
+ * subproblem Psi_k at Y (Section 4, Eq. (Sub-k), Proposition 4.2):
+ *   Psi   = <D + Xt, S + C> + sigma/2 ||Q(S + C)||^2,  S = Y Y'
+ *   G     = Xt + D - sigma R,  R = A*(y(S)) - S - C     (Lemma 3.1)
+ *   z     = diag(G S),  rgrad = 2 (G Y - Diag(z) Y) = 2 X Y
+ * Y: device N x p FP64 with unit rows.  Outputs (each may be NULL):
+ *   psi, rnorm (= ||R||): host scalars; rgrad: device N x p; z: device N;
+ *   y: device m (the per-class means y(S)).
+ * Uses the context's multiplier and sigma.  The evaluated G is kept in the
+ * context and used by later manidsdp_hessvec calls at the same Y.
+ */
+int manidsdp_subproblem_eval(manidsdp_ctx* ctx, const double* Y, int32_t p, double* psi,
+                             double* rgrad, double* z, double* y, double* rnorm);
+
+/*
+ * manidsdp_hessvec - Riemannian Hessian of Psi_k at Y applied to U
+ * (Proposition 4.2, Eq. (4.7)):
+ *   W  = Y U' + U Y',  w = (AA*)^{-1} A(W)
+ *   Ht = 2 G U + 2 sigma (Y (U'Y) + U (Y'Y) - A*(w) Y)      [= 2GU + 2 sigma Q(W) Y]
+ *   HU = Ht - Diag(Ht Y') Y - 2 Diag(z) U
+ * evaluated on P_Y(U) (equal to U for tangent U).  Requires a preceding
+ * manidsdp_subproblem_eval at the same Y (same device pointer and contents).
+ * Y, U, HU: device N x p FP64 (HU may not alias Y or U).  precision selects
+ * MANIDSDP_PREC_FP64 or MANIDSDP_PREC_MIXED for this call.
+ */
+int manidsdp_hessvec(manidsdp_ctx* ctx, const double* Y, const double* U, int32_t p,
+                     double* HU, int32_t precision);
+
+/*
+ * manidsdp_lanczos - extreme eigenpair of the certificate
+ *   X = Xt + D - Diag(z),  z = diag((Xt + D) Y Y')          (Algorithm 1, steps 7-9)
+ * at the context's multiplier and the factor Y (device N x p FP64).  Lanczos
+ * with full FP64 reorthogonalisation, at most k steps (k <= N; k <= 0 uses
+ * params.lanczos_k).  which: MANIDSDP_EIG_MIN or _MAX.  Outputs: *lambda
+ * (host), v (device N, unit norm, first nonzero entry positive; may be NULL),
+ * *steps (host, may be NULL).
+ */
+int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t which, int32_t k,
+                     double* lambda, double* v, int32_t* steps);
+
+/*
+ * manidsdp_solve - Algorithm 1 from the starting matrix Y0 (host or device,
+ * N x p0 FP64, rows normalised by the library) to eta_max <= params.tol or
+ * params.max_outer outer iterations.
+ * Outputs (host or device; each may be NULL):
+ *   Y_out  N x p_cap FP64 with p_cap = params.p_max; the first *p_out columns hold
+ *          the final factor;
+ *   y_out  m FP64 (y at the final S);   z_out N FP64;
+ *   Xt_out N x N FP64 final multiplier; report: host struct.
+ * Returns MANIDSDP_OK when eta_max <= tol, MANIDSDP_E_NOCONV otherwise.
+ * The context's multiplier and sigma are reset to 0 and params.sigma0 at entry.
+ */
+int manidsdp_solve(manidsdp_ctx* ctx, const double* Y0, int32_t p0, double* Y_out,
+                   int32_t* p_out, double* y_out, double* z_out, double* Xt_out,
+                   manidsdp_report* report);
+
+/*
+ * manidsdp_bqp_index_map - host helper: the moment-relaxation data of a binary
+ * quadratic program min x'Qx + c'x, x in {-1,1}^q (Section 3.1).
+ *   order 1: basis [1, x_1..x_q]; order 2: [1, x, x_1x_2, ..., x_{q-1}x_q].
+ *   The class of entry (b, g) is the square-free monomial of the symmetric
+ *   difference of the two basis monomials (x_i^2 = 1), ranked by degree and
+ *   then lexicographically.
+ * Pass idx = NULL to query *N and *m only.  idx: host N x N int32 output.
+ */
+int manidsdp_bqp_index_map(int32_t q, int32_t order, int32_t* N, int64_t* m, int32_t* idx);
+
+/* Right-hand side b (host, m FP64 output) of the BQP relaxation: the
+ * coefficients of x'Qx + c'x modulo x_i^2 = 1 on the canonical monomials:
+ * b[1] = trace(Q), b[x_i] = c_i, b[x_i x_j] = 2 Q_ij (i < j), 0 otherwise.
+ * Q: host q x q symmetric FP64; c: host q FP64 (NULL = 0).  Section 3.1. */
+int manidsdp_bqp_rhs(int32_t q, int32_t order, const double* Q, const double* c, double* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MANIDSDP_H */

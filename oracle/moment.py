@@ -126,7 +126,10 @@ def rhs(q: int, Q: np.ndarray, c: np.ndarray, order: int = 2) -> np.ndarray:
     sum(z) against it."""
     m = num_monomials(q, order)
     b = np.zeros(m)
-    b[0] = np.trace(Q)
+    tr = 0.0
+    for i in range(q):  # left to right, so that the rounding order is fixed
+        tr += float(Q[i, i])
+    b[0] = tr
     b[1:1 + q] = c
     k = 1 + q
     for i in range(q):

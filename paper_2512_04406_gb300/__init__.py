@@ -1,0 +1,227 @@
+"""Python binding of libmanidsdp: the GB300 hot path of ManiDSDP (arXiv 2512.04406).
+
+Thin ctypes marshalling over the C ABI declared in ``include/manidsdp.h``; the
+function names are the C names.  Arrays may be NumPy arrays (host memory) or
+torch tensors (host or CUDA); every computation runs in the library's CUDA
+kernels.  There is no CPU fallback: importing this package fails when the
+shared library has not been built (``python -m paper_2512_04406_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+__all__ = [
+    "ManidsdpError", "Params", "Report", "Context",
+    "manidsdp_default_params", "manidsdp_strerror", "manidsdp_setup", "manidsdp_destroy",
+    "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_subproblem_eval",
+    "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
+    "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
+    "lib_path",
+]
+
+OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+C_ZERO, C_DENSE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+EIG_MIN, EIG_MAX = 0, 1
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"libmanidsdp.so is not built ({_LIB_PATH}); run `python -m paper_2512_04406_gb300.build`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "sigma0", "sigma_min", "sigma_max", "gamma", "kappa1", "kappa2", "tol",
+        "tol_grad_min", "tol_grad_max", "tol_grad_factor", "rank_tol", "neg_tol", "tcg_floor")] + [
+        (n, ctypes.c_int32) for n in (
+            "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
+            "carry_halvings", "lanczos_k", "precision_mode", "verbose", "reserved")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Report(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "eta_p", "eta_d", "eta_g", "value", "pobj", "lambda_min", "lambda_max", "sigma")] + [
+        (n, ctypes.c_int32) for n in (
+            "outer", "rtr_iters", "hessvecs", "p", "lanczos_matvecs", "status", "reserved0",
+            "reserved1")]
+
+    @property
+    def eta_max(self):
+        return max(self.eta_p, self.eta_d, self.eta_g)
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Context(ctypes.c_void_p):
+    """Opaque manidsdp_ctx*."""
+
+
+_P = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_sig = {
+    "manidsdp_default_params": (None, [ctypes.POINTER(Params)]),
+    "manidsdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "manidsdp_setup": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.c_int32, ctypes.c_int64, _P,
+                                      _P, ctypes.c_int32, _P, ctypes.POINTER(Params), _P]),
+    "manidsdp_destroy": (None, [Context]),
+    "manidsdp_set_state": (ctypes.c_int, [Context, _P, ctypes.c_double]),
+    "manidsdp_get_multiplier": (ctypes.c_int, [Context, _P]),
+    "manidsdp_subproblem_eval": (ctypes.c_int, [Context, _P, ctypes.c_int32, _dp, _P, _P, _P,
+                                                _dp]),
+    "manidsdp_hessvec": (ctypes.c_int, [Context, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "manidsdp_lanczos": (ctypes.c_int, [Context, _P, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, _dp, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "manidsdp_solve": (ctypes.c_int, [Context, _P, ctypes.c_int32, _P,
+                                      ctypes.POINTER(ctypes.c_int32), _P, _P, _P,
+                                      ctypes.POINTER(Report)]),
+    "manidsdp_bqp_index_map": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int64), _P]),
+    "manidsdp_bqp_rhs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class ManidsdpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {manidsdp_strerror(status)} ({status})")
+
+
+def _check(st: int, where: str, allow=(OK,)):
+    if st not in allow:
+        raise ManidsdpError(st, where)
+    return st
+
+
+def _ptr(a, dtype=None, writable=False):
+    """Raw address of a contiguous NumPy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        if writable and not a.flags.writeable:
+            raise ValueError("array is read-only")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(a.dtype).replace("torch.", "") != np.dtype(dtype).name:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def manidsdp_default_params() -> Params:
+    p = Params()
+    _lib.manidsdp_default_params(ctypes.byref(p))
+    return p
+
+
+def manidsdp_strerror(status: int) -> str:
+    return _lib.manidsdp_strerror(status).decode()
+
+
+def manidsdp_setup(N: int, m: int, idx, b, c_kind: int = C_ZERO, c_dense=None,
+                   params: Params | None = None, stream: int | None = None) -> Context:
+    ctx = Context()
+    st = _lib.manidsdp_setup(ctypes.byref(ctx), N, m, _ptr(idx, np.int32), _ptr(b, np.float64),
+                             c_kind, _ptr(c_dense, np.float64),
+                             ctypes.byref(params) if params is not None else None, stream)
+    _check(st, "manidsdp_setup")
+    return ctx
+
+
+def manidsdp_destroy(ctx: Context) -> None:
+    _lib.manidsdp_destroy(ctx)
+
+
+def manidsdp_set_state(ctx: Context, Xt=None, sigma: float = 1.0) -> None:
+    _check(_lib.manidsdp_set_state(ctx, _ptr(Xt, np.float64), sigma), "manidsdp_set_state")
+
+
+def manidsdp_get_multiplier(ctx: Context, Xt) -> None:
+    _check(_lib.manidsdp_get_multiplier(ctx, _ptr(Xt, np.float64, True)),
+           "manidsdp_get_multiplier")
+
+
+def manidsdp_subproblem_eval(ctx: Context, Y, p: int, rgrad=None, z=None, y=None):
+    """Returns (psi, ||R||); fills the given device outputs."""
+    psi, rn = ctypes.c_double(), ctypes.c_double()
+    st = _lib.manidsdp_subproblem_eval(ctx, _ptr(Y, np.float64), p, ctypes.byref(psi),
+                                       _ptr(rgrad, np.float64, True), _ptr(z, np.float64, True),
+                                       _ptr(y, np.float64, True), ctypes.byref(rn))
+    _check(st, "manidsdp_subproblem_eval")
+    return psi.value, rn.value
+
+
+def manidsdp_hessvec(ctx: Context, Y, U, p: int, HU, precision: int = PREC_FP64) -> None:
+    st = _lib.manidsdp_hessvec(ctx, _ptr(Y, np.float64), _ptr(U, np.float64), p,
+                               _ptr(HU, np.float64, True), precision)
+    _check(st, "manidsdp_hessvec")
+
+
+def manidsdp_lanczos(ctx: Context, Y, p: int, which: int = EIG_MIN, k: int = 0, v=None):
+    lam = ctypes.c_double()
+    steps = ctypes.c_int32()
+    st = _lib.manidsdp_lanczos(ctx, _ptr(Y, np.float64), p, which, k, ctypes.byref(lam),
+                               _ptr(v, np.float64, True), ctypes.byref(steps))
+    _check(st, "manidsdp_lanczos")
+    return lam.value, steps.value
+
+
+def manidsdp_solve(ctx: Context, Y0, p0: int, Y_out=None, y_out=None, z_out=None, Xt_out=None,
+                   raise_on_noconv: bool = False):
+    """Algorithm 1.  Returns (Report, p_final); status NOCONV is reported in
+    Report.status unless raise_on_noconv."""
+    rep = Report()
+    pout = ctypes.c_int32()
+    st = _lib.manidsdp_solve(ctx, _ptr(Y0, np.float64), p0, _ptr(Y_out, np.float64, True),
+                             ctypes.byref(pout), _ptr(y_out, np.float64, True),
+                             _ptr(z_out, np.float64, True), _ptr(Xt_out, np.float64, True),
+                             ctypes.byref(rep))
+    _check(st, "manidsdp_solve", allow=(OK,) if raise_on_noconv else (OK, E_NOCONV))
+    return rep, pout.value
+
+
+def manidsdp_bqp_index_map(q: int, order: int = 2):
+    """Returns (N, m, idx[N, N] int32) for the BQP moment relaxation of the given order."""
+    N, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.manidsdp_bqp_index_map(q, order, ctypes.byref(N), ctypes.byref(m), None),
+           "manidsdp_bqp_index_map")
+    idx = np.empty((N.value, N.value), dtype=np.int32)
+    _check(_lib.manidsdp_bqp_index_map(q, order, ctypes.byref(N), ctypes.byref(m),
+                                       _ptr(idx, np.int32, True)), "manidsdp_bqp_index_map")
+    return N.value, m.value, idx
+
+
+def manidsdp_bqp_rhs(q: int, Q, c=None, order: int = 2) -> np.ndarray:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    N, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.manidsdp_bqp_index_map(q, order, ctypes.byref(N), ctypes.byref(m), None),
+           "manidsdp_bqp_rhs")
+    b = np.empty(m.value)
+    _check(_lib.manidsdp_bqp_rhs(q, order, _ptr(Q), _ptr(c), _ptr(b, np.float64, True)),
+           "manidsdp_bqp_rhs")
+    return b

@@ -1,0 +1,1003 @@
+// C ABI of the ManiDSDP hot path: context set-up, subproblem evaluation, the
+// Riemannian Hessian-vector product, Lanczos on the certificate, and
+// Algorithm 1 (ALM outer loop around Riemannian trust region with truncated CG).
+// The host here only sequences kernels and takes the scalar decisions (tCG step
+// sizes, trust-region ratio, sigma rule, rank update); every vector and matrix
+// operation runs in the kernels of kernels_seg.cu and kernels_dense.cu.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <stdexcept>
+
+#include "common.cuh"
+
+using namespace mds;
+
+namespace {
+
+struct HostEig {  // eigenpairs of a small symmetric matrix, ascending
+  std::vector<double> w;
+  std::vector<double> V;  // column-major n x n: V[i + n * j] = component i of vector j
+};
+
+// Cyclic Jacobi rotations on a dense symmetric n x n matrix (row-major input).
+HostEig jacobi_eig(const std::vector<double>& A_in, int n) {
+  std::vector<double> A(A_in);
+  std::vector<double> V(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i + size_t(n) * i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double a = A[size_t(i) * n + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[size_t(p) * n + q];
+        if (apq == 0.0) continue;
+        const double app = A[size_t(p) * n + p], aqq = A[size_t(q) * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[size_t(k) * n + p], akq = A[size_t(k) * n + q];
+          A[size_t(k) * n + p] = c * akp - s * akq;
+          A[size_t(k) * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[size_t(p) * n + k], aqk = A[size_t(q) * n + k];
+          A[size_t(p) * n + k] = c * apk - s * aqk;
+          A[size_t(q) * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k + size_t(n) * p], vkq = V[k + size_t(n) * q];
+          V[k + size_t(n) * p] = c * vkp - s * vkq;
+          V[k + size_t(n) * q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return A[size_t(a) * n + a] < A[size_t(b) * n + b]; });
+  HostEig out;
+  out.w.resize(n);
+  out.V.resize(size_t(n) * n);
+  for (int j = 0; j < n; ++j) {
+    out.w[j] = A[size_t(order[j]) * n + order[j]];
+    for (int i = 0; i < n; ++i) out.V[i + size_t(n) * j] = V[i + size_t(n) * order[j]];
+  }
+  return out;
+}
+
+// ---- symmetric tridiagonal T (diagonal a[0..k-1], off-diagonal b[0..k-2]) ----
+int sturm_below(const std::vector<double>& a, const std::vector<double>& b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// i-th smallest eigenvalue (0-based) by bisection on Sturm counts.
+double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int k, int i) {
+  double lo = a[0], hi = a[0];
+  for (int j = 0; j < k; ++j) {
+    const double r = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + (j < k - 1 ? std::fabs(b[j]) : 0.0);
+    lo = std::min(lo, a[j] - r);
+    hi = std::max(hi, a[j] + r);
+  }
+  const double scale = std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
+  for (int it = 0; it < 200 && hi - lo > 1e-17 * scale; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(a, b, k, mid) > i)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Eigenvector of T for eigenvalue theta by inverse iteration (LU without pivoting,
+// tiny pivots replaced), orthogonalised against `prev`.
+std::vector<double> tridiag_vec(const std::vector<double>& a, const std::vector<double>& b, int k,
+                                double theta, const std::vector<std::vector<double>>& prev) {
+  double tn = 0.0;
+  for (int j = 0; j < k; ++j) tn = std::max(tn, std::fabs(a[j]) + (j < k - 1 ? std::fabs(b[j]) : 0.0));
+  const double tiny = 1e-14 * (tn + 1e-300);
+  std::vector<double> x(k), u(k), l(k), d(k);
+  for (int j = 0; j < k; ++j) x[j] = 1.0 + 0.01 * ((j * 7919) % 101);
+  for (int it = 0; it < 4; ++it) {
+    // factor T - theta I = L U with U bidiagonal (d on diagonal, b above)
+    d[0] = a[0] - theta;
+    if (std::fabs(d[0]) < tiny) d[0] = tiny;
+    for (int j = 1; j < k; ++j) {
+      l[j] = b[j - 1] / d[j - 1];
+      d[j] = (a[j] - theta) - l[j] * b[j - 1];
+      if (std::fabs(d[j]) < tiny) d[j] = tiny;
+    }
+    for (int j = 1; j < k; ++j) x[j] -= l[j] * x[j - 1];
+    x[k - 1] /= d[k - 1];
+    for (int j = k - 2; j >= 0; --j) x[j] = (x[j] - b[j] * x[j + 1]) / d[j];
+    for (const auto& pv : prev) {
+      double dp = 0.0;
+      for (int j = 0; j < k; ++j) dp += pv[j] * x[j];
+      for (int j = 0; j < k; ++j) x[j] -= dp * pv[j];
+    }
+    double nrm = 0.0;
+    for (int j = 0; j < k; ++j) nrm += x[j] * x[j];
+    nrm = std::sqrt(nrm);
+    for (int j = 0; j < k; ++j) x[j] /= nrm;
+  }
+  return x;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): the start vector of Lanczos.
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace
+
+struct manidsdp_ctx {
+  int N = 0;
+  int64_t m = 0;
+  int c_kind = 0;
+  manidsdp_params prm{};
+  cudaStream_t s = nullptr;
+  std::vector<void*> allocs;
+  // problem data
+  int32_t* idx = nullptr;
+  double *mult = nullptr, *b = nullptr, *bm = nullptr, *C = nullptr;
+  double normb = 0.0, normC = 0.0;
+  ClassMap cm;
+  // ALM state and N x N work
+  double *XD = nullptr, *G = nullptr, *Gt = nullptr;
+  float *Gf = nullptr, *Gtf = nullptr;
+  // per class
+  double *y = nullptr, *yt = nullptr, *w = nullptr, *piece_buf = nullptr;
+  float* wf = nullptr;
+  // N x pcap
+  int pcap = 0;
+  double *Y = nullptr, *Yt = nullptr, *GY = nullptr, *grad = nullptr, *eta = nullptr,
+         *Heta = nullptr, *r = nullptr, *delta = nullptr, *Hd = nullptr, *Up = nullptr,
+         *Tm = nullptr, *YM = nullptr, *U = nullptr, *tmp = nullptr, *Vn = nullptr;
+  float *Yf = nullptr, *Upf = nullptr, *Tmf = nullptr, *YMf = nullptr;
+  double *z = nullptr, *zt = nullptr;
+  double *M1 = nullptr, *M2 = nullptr;
+  float *M1f = nullptr, *M2f = nullptr;
+  double *part = nullptr, *out2 = nullptr, *dpart = nullptr;
+  void* gws = nullptr;
+  size_t gws_bytes = 0;
+  // Lanczos
+  int kmax = 0;
+  double *LV = nullptr, *lh = nullptr, *lw = nullptr, *ls = nullptr;
+  double* hp = nullptr;  // pinned host scalars
+  // state
+  double sigma = 1.0, xdc = 0.0;
+  bool yf_valid = false;
+  const double* eval_user_Y = nullptr;
+  int eval_p = 0;
+  bool eval_ok = false;
+  double psi = 0.0, r2 = 0.0;
+  // counters
+  int hessvecs = 0, rtr_iters = 0, lanczos_mv = 0;
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(manidsdp_ctx* c, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) throw std::bad_alloc();
+  c->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+void sync(manidsdp_ctx* c) { MDS_CUDA(cudaStreamSynchronize(c->s)); }
+
+// Deterministic dot products of up to three pairs of length n; results on the host.
+void dots(manidsdp_ctx* c, size_t n, int k, const double* x0, const double* y0, double* out,
+          const double* x1 = nullptr, const double* y1 = nullptr, const double* x2 = nullptr,
+          const double* y2 = nullptr) {
+  const double* xs[3] = {x0, x1, x2};
+  const double* ys[3] = {y0, y1, y2};
+  launch_dots(n, k, xs, ys, c->dpart, c->s);
+  MDS_CUDA(cudaMemcpyAsync(c->hp, c->dpart + 3 * kRedBlocks, k * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->s));
+  sync(c);
+  for (int i = 0; i < k; ++i) out[i] = c->hp[i];
+}
+
+// Psi, y and G (and Gf in mixed mode) at Y.
+void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, float* Gf,
+              double* psi, double* r2) {
+  launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y, c->s);
+  launch_gpass(c->N, p, 0, Y, c->idx, y, c->C, c->sigma, c->XD, G, Gf, c->part, c->out2, c->s);
+  MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  sync(c);
+  *r2 = c->hp[0];
+  *psi = c->hp[1] + c->xdc + 0.5 * c->sigma * c->hp[0];
+}
+
+// GY = G Y, z = diag(G S), grad = 2 (GY - Diag(z) Y); returns ||grad||.
+double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
+  const int N = c->N;
+  launch_gemm<double>(N, p, N, G, N, Y, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0, nullptr,
+                      c->gws, c->gws_bytes, c->s);
+  launch_rowdot(N, p, c->GY, Y, c->z, c->s);
+  launch_grad_from_gy(N, p, c->GY, c->z, Y, c->grad, c->s);
+  double gg;
+  dots(c, size_t(N) * p, 1, c->grad, c->grad, &gg);
+  return std::sqrt(gg);
+}
+
+// HU = Hess Psi(Y)[P_Y(U)] using G, Gf and z of the last evaluation at Y.
+void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* HU, int prec) {
+  const int N = c->N;
+  const size_t np = size_t(N) * p;
+  launch_proj_tangent(N, p, Y, U, c->Up, c->s);
+  if (prec == MANIDSDP_PREC_FP64) {
+    launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
+                               c->s);
+    launch_gemm<double>(N, p, N, c->G, N, c->Up, p, c->Tm, p, 1.0, 0.0, c->idx, c->w, -c->sigma,
+                        Y, c->gws, c->gws_bytes, c->s);
+    launch_gram<double>(N, p, p, c->Up, Y, c->M1, c->s);
+    launch_gram<double>(N, p, p, Y, Y, c->M2, c->s);
+    launch_gemm<double>(N, p, p, Y, p, c->M1, p, c->YM, p, 1.0, 0.0, nullptr, nullptr, 0.0,
+                        nullptr, c->gws, c->gws_bytes, c->s);
+    launch_gemm<double>(N, p, p, c->Up, p, c->M2, p, c->YM, p, 1.0, 1.0, nullptr, nullptr, 0.0,
+                        nullptr, c->gws, c->gws_bytes, c->s);
+    launch_hess_epilogue<double>(N, p, c->Tm, c->YM, Y, c->Up, c->z, c->sigma, HU, c->s);
+  } else {
+    if (!c->yf_valid) {
+      launch_to_float(np, Y, c->Yf, c->s);
+      c->yf_valid = true;
+    }
+    launch_to_float(np, c->Up, c->Upf, c->s);
+    float* pbf = reinterpret_cast<float*>(c->piece_buf);
+    launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, c->s);
+    launch_gemm<float>(N, p, N, c->Gf, N, c->Upf, p, c->Tmf, p, 1.0f, 0.0f, c->idx, c->wf,
+                       float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
+    launch_gram<float>(N, p, p, c->Upf, c->Yf, c->M1f, c->s);
+    launch_gram<float>(N, p, p, c->Yf, c->Yf, c->M2f, c->s);
+    launch_gemm<float>(N, p, p, c->Yf, p, c->M1f, p, c->YMf, p, 1.0f, 0.0f, nullptr, nullptr,
+                       0.0f, nullptr, c->gws, c->gws_bytes, c->s);
+    launch_gemm<float>(N, p, p, c->Upf, p, c->M2f, p, c->YMf, p, 1.0f, 1.0f, nullptr, nullptr,
+                       0.0f, nullptr, c->gws, c->gws_bytes, c->s);
+    launch_hess_epilogue<float>(N, p, c->Tmf, c->YMf, c->Yf, c->Upf, c->z, c->sigma, HU, c->s);
+  }
+  c->hessvecs++;
+}
+
+struct LanczosOut {
+  std::vector<double> lo;  // smallest Ritz values (ascending), those returned
+  double hi = 0.0;
+  int steps = 0;
+  int nvec = 0;  // Ritz vectors written to c->Vn (N x nvec, row-major)
+};
+
+// Lanczos with full reorthogonalisation on X = XD - Diag(z) (z on device).
+LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
+  const int N = c->N;
+  int k = std::min(std::min(kcap, c->kmax), N);
+  if (k < 1) k = 1;
+  std::vector<double> v0(N);
+  double nrm = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const uint64_t u = splitmix64(0x5EEDull + uint64_t(i));
+    v0[i] = (double(u >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+    nrm += v0[i] * v0[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (int i = 0; i < N; ++i) v0[i] /= nrm;
+  MDS_CUDA(cudaMemcpyAsync(c->LV, v0.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->s));
+  std::vector<double> al, be;
+  int steps = k;
+  double res_lo = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double* vj = c->LV + size_t(j) * N;
+    launch_gemv_cert(N, c->XD, z, vj, c->lw, c->s);
+    c->lanczos_mv++;
+    launch_basis_dots(N, j + 1, c->LV, c->lw, c->lh, c->s);
+    MDS_CUDA(cudaMemcpyAsync(c->hp + 8, c->lh + j, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    launch_basis_update(N, j + 1, c->LV, c->lh, c->lw, c->s);
+    launch_basis_dots(N, j + 1, c->LV, c->lw, c->lh, c->s);
+    launch_basis_update(N, j + 1, c->LV, c->lh, c->lw, c->s);
+    double bb;
+    dots(c, N, 1, c->lw, c->lw, &bb);  // synchronises; hp[8] now holds alpha_j
+    const double alpha = c->hp[8];
+    const double beta = std::sqrt(bb);
+    al.push_back(alpha);
+    if (beta <= 1e-14 * std::max(1.0, std::fabs(alpha)) || j == k - 1) {
+      steps = j + 1;
+      break;
+    }
+    be.push_back(beta);
+    launch_axpby(N, 1.0 / beta, c->lw, 0.0, nullptr, c->LV + size_t(j + 1) * N, c->s);
+    // convergence of the extreme Ritz pairs every 10 steps
+    if ((j + 1) % 10 == 0) {
+      const int kk = j + 1;
+      const double tlo = tridiag_eig(al, be, kk, 0);
+      const double thi = tridiag_eig(al, be, kk, kk - 1);
+      const auto slo = tridiag_vec(al, be, kk, tlo, {});
+      const auto shi = tridiag_vec(al, be, kk, thi, {});
+      const double scale = std::max(std::fabs(tlo), std::fabs(thi)) + 1e-300;
+      res_lo = beta * std::fabs(slo[kk - 1]);
+      const double res_hi = beta * std::fabs(shi[kk - 1]);
+      if (res_lo <= 1e-10 * scale && res_hi <= 1e-6 * scale) {
+        steps = kk;
+        break;
+      }
+    }
+  }
+  LanczosOut out;
+  out.steps = steps;
+  const int kk = steps;
+  std::vector<double> bt(be.begin(), be.begin() + std::max(0, kk - 1));
+  std::vector<double> at(al.begin(), al.begin() + kk);
+  out.hi = tridiag_eig(at, bt, kk, kk - 1);
+  const int ns = std::min(std::min(n_small, kk), c->pcap);
+  std::vector<std::vector<double>> svecs;
+  for (int i = 0; i < ns; ++i) {
+    const double th = tridiag_eig(at, bt, kk, i);
+    out.lo.push_back(th);
+    svecs.push_back(tridiag_vec(at, bt, kk, th, svecs));
+  }
+  // Ritz vectors into Vn (row-major N x ns): column i = sum_j s_i[j] v_j
+  std::vector<double> neg(kk);
+  for (int i = 0; i < ns; ++i) {
+    for (int j = 0; j < kk; ++j) neg[j] = -svecs[i][j];
+    MDS_CUDA(cudaMemcpyAsync(c->lh, neg.data(), kk * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    MDS_CUDA(cudaMemsetAsync(c->lw, 0, N * sizeof(double), c->s));
+    launch_basis_update(N, kk, c->LV, c->lh, c->lw, c->s);
+    // sign: first nonzero entry positive
+    MDS_CUDA(cudaMemcpyAsync(c->ls, c->lw, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    std::vector<double> hv(N);
+    MDS_CUDA(cudaMemcpyAsync(hv.data(), c->lw, N * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    sync(c);
+    double sgn = 1.0;
+    for (int t = 0; t < N; ++t)
+      if (std::fabs(hv[t]) > 1e-14) {
+        sgn = hv[t] < 0 ? -1.0 : 1.0;
+        break;
+      }
+    launch_axpby(N, sgn, c->lw, 0.0, nullptr, c->ls, c->s);
+    launch_set_cols(N, ns, i, 1, c->ls, c->Vn, c->s);
+  }
+  out.nvec = ns;
+  sync(c);
+  return out;
+}
+
+void default_params(manidsdp_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->sigma0 = 1.0;
+  p->sigma_min = 1e-3;
+  p->sigma_max = 1e6;
+  p->gamma = 2.0;
+  p->kappa1 = 0.1;
+  p->kappa2 = 10.0;
+  p->tol = 1e-8;
+  p->tol_grad_min = 1e-11;
+  p->tol_grad_max = 1e-2;
+  p->tol_grad_factor = 0.1;
+  p->rank_tol = 1e-10;
+  p->neg_tol = 1e-10;
+  p->tcg_floor = 1e-10;
+  p->p0 = 2;
+  p->p_min = 2;
+  p->p_max = 256;
+  p->delta_max = 8;
+  p->max_outer = 300;
+  p->max_rtr = 200;
+  p->max_tcg = 500;
+  p->carry_halvings = 30;
+  p->lanczos_k = 300;
+  p->precision_mode = MANIDSDP_PREC_FP64;
+  p->verbose = 0;
+}
+
+struct NonFinite {};
+
+int guard(const std::function<int()>& f) {
+  try {
+    return f();
+  } catch (const NonFinite&) {
+    return MANIDSDP_E_NONFINITE;
+  } catch (const DeviceError&) {
+    return MANIDSDP_E_CUDA;
+  } catch (const std::bad_alloc&) {
+    return MANIDSDP_E_NOMEM;
+  } catch (...) {
+    return MANIDSDP_E_CUDA;
+  }
+}
+
+void release(manidsdp_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->hp) cudaFreeHost(c->hp);
+  c->hp = nullptr;
+}
+
+// Reset the ALM state: XD = Xt + D with Xt given (device) or zero; sigma.
+void set_state(manidsdp_ctx* c, const double* Xt_dev, double sigma) {
+  const size_t NN = size_t(c->N) * c->N;
+  if (Xt_dev == nullptr) {
+    MDS_CUDA(cudaMemsetAsync(c->G, 0, NN * sizeof(double), c->s));
+    launch_xd_from_xt(NN, 0, c->G, c->idx, c->bm, c->XD, c->s);
+  } else {
+    launch_xd_from_xt(NN, 0, Xt_dev, c->idx, c->bm, c->XD, c->s);
+  }
+  c->sigma = sigma;
+  c->xdc = 0.0;
+  if (c->C != nullptr) dots(c, NN, 1, c->XD, c->C, &c->xdc);
+  c->eval_ok = false;
+  sync(c);
+}
+
+}  // namespace
+
+// ============================== C ABI ========================================
+extern "C" {
+
+void manidsdp_default_params(manidsdp_params* params) {
+  if (params) default_params(params);
+}
+
+const char* manidsdp_strerror(int status) {
+  switch (status) {
+    case MANIDSDP_OK: return "ok";
+    case MANIDSDP_E_ARG: return "invalid argument";
+    case MANIDSDP_E_NONFINITE: return "non-finite value";
+    case MANIDSDP_E_NOCONV: return "iteration limit reached before the KKT tolerance";
+    case MANIDSDP_E_TIMEOUT: return "device-side wait timed out";
+    case MANIDSDP_E_CUDA: return "CUDA runtime error";
+    case MANIDSDP_E_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* idx,
+                   const double* b, int32_t c_kind, const double* c_dense,
+                   const manidsdp_params* params, void* stream) {
+  if (ctx_out == nullptr || idx == nullptr || b == nullptr || N < 1 || N > kMaxN || m < 1 ||
+      m > int64_t(N) * N || (c_kind != MANIDSDP_C_ZERO && c_kind != MANIDSDP_C_DENSE) ||
+      (c_kind == MANIDSDP_C_DENSE && c_dense == nullptr))
+    return MANIDSDP_E_ARG;
+  manidsdp_params prm;
+  if (params)
+    prm = *params;
+  else
+    default_params(&prm);
+  if (prm.p_max < 1 || prm.p_max > 4096 || prm.p0 < 1 || prm.p0 > prm.p_max || prm.p_min < 1 ||
+      prm.delta_max < 0 || prm.lanczos_k < 1)
+    return MANIDSDP_E_ARG;
+  // validate the index map and build the per-class inverse map on the host
+  const size_t NN = size_t(N) * N;
+  std::vector<int32_t> count(m, 0);
+  for (int r = 0; r < N; ++r)
+    for (int c2 = 0; c2 < N; ++c2) {
+      const int32_t a = idx[size_t(r) * N + c2];
+      if (a < 0 || a >= m || a != idx[size_t(c2) * N + r]) return MANIDSDP_E_ARG;
+      count[a]++;
+    }
+  for (int64_t a = 0; a < m; ++a)
+    if (count[a] == 0) return MANIDSDP_E_ARG;  // A A* singular (Assumption 2)
+  std::vector<double> mult(m);
+  for (int64_t a = 0; a < m; ++a) mult[a] = double(count[a]);
+  std::vector<int32_t> ucount(m + 1, 0);
+  for (int r = 0; r < N; ++r)
+    for (int c2 = r; c2 < N; ++c2) ucount[idx[size_t(r) * N + c2] + 1]++;
+  for (int64_t a = 0; a < m; ++a) ucount[a + 1] += ucount[a];
+  const int32_t n_ent = ucount[m];
+  std::vector<uint32_t> ent(n_ent);
+  {
+    std::vector<int32_t> pos(ucount.begin(), ucount.end() - 1);
+    for (int r = 0; r < N; ++r)
+      for (int c2 = r; c2 < N; ++c2)
+        ent[pos[idx[size_t(r) * N + c2]]++] = (uint32_t(r) << 16) | uint32_t(c2);
+  }
+  std::vector<int32_t> pstart, pclass, mclass, mrange;
+  for (int64_t a = 0; a < m; ++a) {
+    const int32_t e0 = ucount[a], e1 = ucount[a + 1];
+    const int np = (e1 - e0 + kPieceLen - 1) / kPieceLen;
+    if (np > 1) {
+      mclass.push_back(int32_t(a));
+      mrange.push_back(int32_t(pstart.size()));
+      mrange.push_back(int32_t(pstart.size()) + np);
+    }
+    for (int t = 0; t < np; ++t) {
+      pstart.push_back(e0 + t * kPieceLen);
+      pclass.push_back(np > 1 ? -1 : int32_t(a));
+    }
+  }
+  pstart.push_back(n_ent);
+
+  manidsdp_ctx* c = new (std::nothrow) manidsdp_ctx();
+  if (c == nullptr) return MANIDSDP_E_NOMEM;
+  int st = guard([&]() -> int {
+    c->N = N;
+    c->m = m;
+    c->c_kind = c_kind;
+    c->prm = prm;
+    c->s = static_cast<cudaStream_t>(stream);
+    MDS_CUDA(cudaMallocHost(&c->hp, 64 * sizeof(double)));
+    c->idx = dalloc<int32_t>(c, NN);
+    MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+    c->mult = dalloc<double>(c, m);
+    MDS_CUDA(cudaMemcpyAsync(c->mult, mult.data(), m * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    c->b = dalloc<double>(c, m);
+    MDS_CUDA(cudaMemcpyAsync(c->b, b, m * sizeof(double), cudaMemcpyDefault, c->s));
+    std::vector<double> hb(m), hbm(m);
+    MDS_CUDA(cudaMemcpyAsync(hb.data(), c->b, m * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    sync(c);
+    double nb = 0.0;
+    for (int64_t a = 0; a < m; ++a) {
+      hbm[a] = hb[a] / mult[a];
+      nb += hb[a] * hb[a];
+    }
+    c->normb = std::sqrt(nb);
+    c->bm = dalloc<double>(c, m);
+    MDS_CUDA(cudaMemcpyAsync(c->bm, hbm.data(), m * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    if (c_kind == MANIDSDP_C_DENSE) {
+      c->C = dalloc<double>(c, NN);
+      MDS_CUDA(cudaMemcpyAsync(c->C, c_dense, NN * sizeof(double), cudaMemcpyDefault, c->s));
+    }
+    // inverse map
+    c->cm.n_entries = n_ent;
+    c->cm.n_pieces = int32_t(pclass.size());
+    c->cm.n_multi = int32_t(mclass.size());
+    c->cm.ent = dalloc<uint32_t>(c, n_ent);
+    c->cm.piece_start = dalloc<int32_t>(c, pstart.size());
+    c->cm.piece_class = dalloc<int32_t>(c, pclass.size());
+    c->cm.multi_class = dalloc<int32_t>(c, mclass.size());
+    c->cm.multi_range = dalloc<int32_t>(c, mrange.size());
+    MDS_CUDA(cudaMemcpyAsync(c->cm.ent, ent.data(), n_ent * sizeof(uint32_t), cudaMemcpyHostToDevice, c->s));
+    MDS_CUDA(cudaMemcpyAsync(c->cm.piece_start, pstart.data(), pstart.size() * 4, cudaMemcpyHostToDevice, c->s));
+    MDS_CUDA(cudaMemcpyAsync(c->cm.piece_class, pclass.data(), pclass.size() * 4, cudaMemcpyHostToDevice, c->s));
+    if (!mclass.empty()) {
+      MDS_CUDA(cudaMemcpyAsync(c->cm.multi_class, mclass.data(), mclass.size() * 4, cudaMemcpyHostToDevice, c->s));
+      MDS_CUDA(cudaMemcpyAsync(c->cm.multi_range, mrange.data(), mrange.size() * 4, cudaMemcpyHostToDevice, c->s));
+    }
+    // N x N work
+    c->XD = dalloc<double>(c, NN);
+    c->G = dalloc<double>(c, NN);
+    c->Gt = dalloc<double>(c, NN);
+    c->Gf = dalloc<float>(c, NN);
+    c->Gtf = dalloc<float>(c, NN);
+    // per class
+    c->y = dalloc<double>(c, m);
+    c->yt = dalloc<double>(c, m);
+    c->w = dalloc<double>(c, m);
+    c->wf = dalloc<float>(c, m);
+    c->piece_buf = dalloc<double>(c, pclass.size());
+    // N x pcap
+    c->pcap = prm.p_max;
+    const size_t np = size_t(N) * c->pcap;
+    double** dbufs[] = {&c->Y, &c->Yt, &c->GY, &c->grad, &c->eta, &c->Heta, &c->r, &c->delta,
+                        &c->Hd, &c->Up, &c->Tm, &c->YM, &c->U, &c->tmp, &c->Vn};
+    for (double** pp : dbufs) *pp = dalloc<double>(c, np);
+    float** fbufs[] = {&c->Yf, &c->Upf, &c->Tmf, &c->YMf};
+    for (float** pp : fbufs) *pp = dalloc<float>(c, np);
+    c->z = dalloc<double>(c, N);
+    c->zt = dalloc<double>(c, N);
+    const size_t pp2 = size_t(c->pcap) * c->pcap;
+    c->M1 = dalloc<double>(c, pp2);
+    c->M2 = dalloc<double>(c, pp2);
+    c->M1f = dalloc<float>(c, pp2);
+    c->M2f = dalloc<float>(c, pp2);
+    c->part = dalloc<double>(c, gpass_partials(N));
+    c->out2 = dalloc<double>(c, 2);
+    c->dpart = dalloc<double>(c, 3 * kRedBlocks + 3);
+    c->gws_bytes = (np + size_t(2) * 304 * 4096) * sizeof(double);
+    c->gws = dalloc<double>(c, c->gws_bytes / sizeof(double));
+    if (c->C != nullptr) {
+      double cc;
+      dots(c, NN, 1, c->C, c->C, &cc);
+      c->normC = std::sqrt(cc);
+    }
+    c->kmax = std::min(std::max(prm.lanczos_k, 1), N);
+    c->LV = dalloc<double>(c, size_t(c->kmax + 1) * N);
+    c->lh = dalloc<double>(c, c->kmax + 1);
+    c->lw = dalloc<double>(c, N);
+    c->ls = dalloc<double>(c, N);
+    set_state(c, nullptr, prm.sigma0);
+    return MANIDSDP_OK;
+  });
+  if (st != MANIDSDP_OK) {
+    release(c);
+    delete c;
+    return st;
+  }
+  *ctx_out = c;
+  return MANIDSDP_OK;
+}
+
+void manidsdp_destroy(manidsdp_ctx* ctx) {
+  if (ctx == nullptr) return;
+  cudaStreamSynchronize(ctx->s);
+  release(ctx);
+  delete ctx;
+}
+
+int manidsdp_set_state(manidsdp_ctx* c, const double* Xt, double sigma) {
+  if (c == nullptr || !(sigma > 0.0)) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    if (Xt != nullptr) {
+      const size_t NN = size_t(c->N) * c->N;
+      MDS_CUDA(cudaMemcpyAsync(c->Gt, Xt, NN * sizeof(double), cudaMemcpyDefault, c->s));
+      set_state(c, c->Gt, sigma);
+    } else {
+      set_state(c, nullptr, sigma);
+    }
+    return MANIDSDP_OK;
+  });
+}
+
+int manidsdp_get_multiplier(manidsdp_ctx* c, double* Xt) {
+  if (c == nullptr || Xt == nullptr) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    const size_t NN = size_t(c->N) * c->N;
+    launch_xd_from_xt(NN, 1, c->XD, c->idx, c->bm, c->Gt, c->s);
+    MDS_CUDA(cudaMemcpyAsync(Xt, c->Gt, NN * sizeof(double), cudaMemcpyDefault, c->s));
+    c->eval_ok = false;
+    sync(c);
+    return MANIDSDP_OK;
+  });
+}
+
+int manidsdp_subproblem_eval(manidsdp_ctx* c, const double* Y, int32_t p, double* psi,
+                             double* rgrad, double* z, double* y, double* rnorm) {
+  if (c == nullptr || Y == nullptr || p < 1 || p > c->pcap) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    const size_t np = size_t(c->N) * p;
+    MDS_CUDA(cudaMemcpyAsync(c->Y, Y, np * sizeof(double), cudaMemcpyDefault, c->s));
+    double ps, r2;
+    evaluate(c, c->Y, p, c->y, c->G, c->Gf, &ps, &r2);
+    gradient(c, c->Y, p, c->G);
+    c->yf_valid = false;
+    c->eval_ok = true;
+    c->eval_user_Y = Y;
+    c->eval_p = p;
+    if (psi) *psi = ps;
+    if (rnorm) *rnorm = std::sqrt(r2);
+    if (rgrad) MDS_CUDA(cudaMemcpyAsync(rgrad, c->grad, np * sizeof(double), cudaMemcpyDefault, c->s));
+    if (z) MDS_CUDA(cudaMemcpyAsync(z, c->z, c->N * sizeof(double), cudaMemcpyDefault, c->s));
+    if (y) MDS_CUDA(cudaMemcpyAsync(y, c->y, c->m * sizeof(double), cudaMemcpyDefault, c->s));
+    sync(c);
+    return MANIDSDP_OK;
+  });
+}
+
+int manidsdp_hessvec(manidsdp_ctx* c, const double* Y, const double* U, int32_t p, double* HU,
+                     int32_t precision) {
+  if (c == nullptr || Y == nullptr || U == nullptr || HU == nullptr || p < 1 || p > c->pcap ||
+      (precision != MANIDSDP_PREC_FP64 && precision != MANIDSDP_PREC_MIXED))
+    return MANIDSDP_E_ARG;
+  if (!c->eval_ok || c->eval_user_Y != Y || c->eval_p != p) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    const size_t np = size_t(c->N) * p;
+    MDS_CUDA(cudaMemcpyAsync(c->delta, U, np * sizeof(double), cudaMemcpyDefault, c->s));
+    hessvec(c, c->Y, c->delta, p, c->Hd, precision);
+    MDS_CUDA(cudaMemcpyAsync(HU, c->Hd, np * sizeof(double), cudaMemcpyDefault, c->s));
+    sync(c);
+    return MANIDSDP_OK;
+  });
+}
+
+int manidsdp_lanczos(manidsdp_ctx* c, const double* Y, int32_t p, int32_t which, int32_t k,
+                     double* lambda, double* v, int32_t* steps) {
+  if (c == nullptr || Y == nullptr || p < 1 || p > c->pcap || lambda == nullptr ||
+      (which != MANIDSDP_EIG_MIN && which != MANIDSDP_EIG_MAX))
+    return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    const int N = c->N;
+    const size_t np = size_t(N) * p;
+    MDS_CUDA(cudaMemcpyAsync(c->tmp, Y, np * sizeof(double), cudaMemcpyDefault, c->s));
+    launch_gemm<double>(N, p, N, c->XD, N, c->tmp, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0,
+                        nullptr, c->gws, c->gws_bytes, c->s);
+    launch_rowdot(N, p, c->GY, c->tmp, c->zt, c->s);
+    LanczosOut lo = lanczos(c, c->zt, k > 0 ? k : c->prm.lanczos_k, 1);
+    if (which == MANIDSDP_EIG_MIN) {
+      *lambda = lo.lo[0];
+      if (v) MDS_CUDA(cudaMemcpyAsync(v, c->Vn, N * sizeof(double), cudaMemcpyDefault, c->s));
+    } else {
+      *lambda = lo.hi;
+      if (v) return MANIDSDP_E_ARG;  // only the smallest pair carries a vector
+    }
+    if (steps) *steps = lo.steps;
+    c->eval_ok = false;
+    sync(c);
+    return MANIDSDP_OK;
+  });
+}
+
+}  // extern "C"
+
+// ============================== Algorithm 1 ==================================
+namespace {
+
+struct TcgOut {
+  int iters;
+  bool boundary;
+};
+
+// Truncated CG on the trust-region model at c->Y (gradient in c->grad).
+TcgOut tcg(manidsdp_ctx* c, int p, double Delta) {
+  const int N = c->N;
+  const size_t n = size_t(N) * p;
+  const manidsdp_params& P = c->prm;
+  MDS_CUDA(cudaMemsetAsync(c->eta, 0, n * sizeof(double), c->s));
+  MDS_CUDA(cudaMemsetAsync(c->Heta, 0, n * sizeof(double), c->s));
+  MDS_CUDA(cudaMemcpyAsync(c->r, c->grad, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  launch_axpby(n, -1.0, c->grad, 0.0, nullptr, c->delta, c->s);
+  double rr;
+  dots(c, n, 1, c->r, c->r, &rr);
+  const double r0 = std::sqrt(rr);
+  double ee = 0.0, ed = 0.0, dd = rr;
+  const double target = r0 * std::max(std::min(std::pow(r0, 1.0), 0.1), P.tcg_floor);
+  for (int j = 1; j <= P.max_tcg; ++j) {
+    hessvec(c, c->Y, c->delta, p, c->Hd, P.precision_mode);
+    double kap;
+    dots(c, n, 1, c->delta, c->Hd, &kap);
+    const double alpha = kap != 0.0 ? rr / kap : INFINITY;
+    const double ee_new = ee + 2.0 * alpha * ed + alpha * alpha * dd;
+    if (kap <= 0.0 || ee_new >= Delta * Delta) {
+      const double tau = (-ed + std::sqrt(ed * ed + dd * (Delta * Delta - ee))) / dd;
+      launch_axpby(n, tau, c->delta, 1.0, c->eta, c->eta, c->s);
+      launch_axpby(n, tau, c->Hd, 1.0, c->Heta, c->Heta, c->s);
+      return {j, true};
+    }
+    launch_axpby(n, alpha, c->delta, 1.0, c->eta, c->eta, c->s);
+    launch_axpby(n, alpha, c->Hd, 1.0, c->Heta, c->Heta, c->s);
+    launch_axpby(n, alpha, c->Hd, 1.0, c->r, c->r, c->s);
+    ee = ee_new;
+    double rr_new;
+    dots(c, n, 1, c->r, c->r, &rr_new);
+    if (std::sqrt(rr_new) <= target) return {j, false};
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    launch_axpby(n, -1.0, c->r, beta, c->delta, c->delta, c->s);
+    ed = beta * (ed + alpha * dd);
+    dd = rr + beta * beta * dd;
+  }
+  return {P.max_tcg, false};
+}
+
+struct RtrOut {
+  int iters;
+  double gnorm;
+};
+
+// Riemannian trust region on Psi_k from c->Y; leaves y, G, z, grad at the final Y.
+RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
+  const int N = c->N;
+  const size_t n = size_t(N) * p;
+  const manidsdp_params& P = c->prm;
+  const double Delta_bar = M_PI * std::sqrt(double(N));
+  double Delta = Delta_bar / 8.0;
+  double fx, r2;
+  float* gf = P.precision_mode == MANIDSDP_PREC_MIXED ? c->Gf : nullptr;
+  evaluate(c, c->Y, p, c->y, c->G, gf, &fx, &r2);
+  c->yf_valid = false;
+  double gn = gradient(c, c->Y, p, c->G);
+  int it = 0;
+  for (; it < P.max_rtr; ++it) {
+    if (gn <= tol_grad) break;
+    TcgOut t = tcg(c, p, Delta);
+    double d2[2];
+    dots(c, n, 2, c->grad, c->eta, d2, c->eta, c->Heta);
+    const double model_dec = -(d2[0] + 0.5 * d2[1]);
+    launch_retract(N, p, c->Y, c->eta, 1.0, c->Yt, c->s);
+    double f_new, r2n;
+    evaluate(c, c->Yt, p, c->yt, c->Gt, gf ? c->Gtf : nullptr, &f_new, &r2n);
+    const double reg = std::max(1.0, std::fabs(fx)) * 1e3 * 2.220446049250313e-16;
+    const double rho = (model_dec + reg > 0.0) ? (fx - f_new + reg) / (model_dec + reg) : -INFINITY;
+    if (!std::isfinite(f_new)) throw NonFinite{};
+    if (rho < 0.25)
+      Delta /= 4.0;
+    else if (rho > 0.75 && t.boundary)
+      Delta = std::min(2.0 * Delta, Delta_bar);
+    if (rho > 0.1) {
+      std::swap(c->Y, c->Yt);
+      std::swap(c->G, c->Gt);
+      std::swap(c->Gf, c->Gtf);
+      gf = P.precision_mode == MANIDSDP_PREC_MIXED ? c->Gf : nullptr;
+      std::swap(c->y, c->yt);
+      fx = f_new;
+      c->yf_valid = false;
+      gn = gradient(c, c->Y, p, c->G);
+    }
+  }
+  c->rtr_iters += it;
+  c->psi = fx;
+  return {it, gn};
+}
+
+// Row-major N x p_old -> N x p_new in place through c->tmp (zero-padded columns).
+void relayout(manidsdp_ctx* c, double* buf, int p_old, int p_new) {
+  launch_pad_cols(c->N, p_old, p_new, buf, c->tmp, c->s);
+  MDS_CUDA(cudaMemcpyAsync(buf, c->tmp, size_t(c->N) * p_new * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->s));
+}
+
+}  // namespace
+
+extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, double* Y_out,
+                              int32_t* p_out, double* y_out, double* z_out, double* Xt_out,
+                              manidsdp_report* report) {
+  if (c == nullptr || Y0 == nullptr || p0 < 1 || p0 > c->pcap) return MANIDSDP_E_ARG;
+  int status = MANIDSDP_E_NOCONV;
+  manidsdp_report rep{};
+  int gst = guard([&]() -> int {
+    const int N = c->N;
+    const manidsdp_params& P = c->prm;
+    c->hessvecs = c->rtr_iters = c->lanczos_mv = 0;
+    set_state(c, nullptr, P.sigma0);
+    int p = p0;
+    MDS_CUDA(cudaMemcpyAsync(c->tmp, Y0, size_t(N) * p * sizeof(double), cudaMemcpyDefault, c->s));
+    launch_retract(N, p, c->tmp, c->tmp, 0.0, c->Y, c->s);
+    bool have_U = false;
+    int U_cols = 0;
+    double rscale = -1.0;
+    double sigma = P.sigma0;
+    for (int k = 0; k < P.max_outer; ++k) {
+      c->sigma = sigma;
+      // step 3a: the carried direction U = [0, V]
+      if (have_U) {
+        double f0, r2;
+        evaluate(c, c->Y, p, c->y, c->G, nullptr, &f0, &r2);
+        c->yf_valid = false;
+        gradient(c, c->Y, p, c->G);
+        hessvec(c, c->Y, c->U, p, c->Hd, MANIDSDP_PREC_FP64);
+        double curv;
+        dots(c, size_t(N) * p, 1, c->U, c->Hd, &curv);
+        bool moved = false;
+        if (curv < 0.0) {
+          double t = std::sqrt(double(N));
+          for (int i = 0; i < P.carry_halvings; ++i) {
+            launch_retract(N, p, c->Y, c->U, t, c->Yt, c->s);
+            double ft, r2t;
+            evaluate(c, c->Yt, p, c->yt, c->Gt, nullptr, &ft, &r2t);
+            if (ft <= f0 - 1e-4 * 0.5 * t * t * std::fabs(curv)) {
+              std::swap(c->Y, c->Yt);
+              moved = true;
+              break;
+            }
+            t *= 0.5;
+          }
+        }
+        if (!moved) {
+          launch_pad_cols(N, p, p - U_cols, c->Y, c->tmp, c->s);  // keep the first p-U_cols columns
+          p -= U_cols;
+          MDS_CUDA(cudaMemcpyAsync(c->Y, c->tmp, size_t(N) * p * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->s));
+        }
+        have_U = false;
+      }
+      // step 3b: RTR on Psi_k
+      const double tol_k = rscale < 0.0 ? P.tol_grad_max
+                                        : std::max(P.tol_grad_min,
+                                                   std::min(P.tol_grad_max, P.tol_grad_factor * rscale));
+      RtrOut ro = rtr(c, p, tol_k);
+      // steps 4-8: y at the final Y is in c->y; Xt <- Xt - sigma R
+      launch_gpass(N, p, 1, c->Y, c->idx, c->y, c->C, sigma, c->XD, nullptr, nullptr, c->part,
+                   c->out2, c->s);
+      MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+      sync(c);
+      const double rnorm = std::sqrt(c->hp[0]);
+      const double sum_z = c->hp[1];
+      if (c->C != nullptr) dots(c, size_t(N) * N, 1, c->XD, c->C, &c->xdc);
+      launch_gemm<double>(N, p, N, c->XD, N, c->Y, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0,
+                          nullptr, c->gws, c->gws_bytes, c->s);
+      launch_rowdot(N, p, c->GY, c->Y, c->z, c->s);
+      // step 9: extreme eigenpairs of X
+      LanczosOut lo = lanczos(c, c->z, P.lanczos_k, std::max(1, P.delta_max));
+      double by;
+      dots(c, c->m, 1, c->b, c->y, &by);
+      rep.eta_p = rnorm / (1.0 + c->normC);
+      rep.eta_d = std::max(0.0, -lo.lo[0]) / (1.0 + std::fabs(lo.hi));
+      rep.pobj = sum_z + c->xdc;
+      rep.value = by;
+      rep.eta_g = std::fabs(rep.pobj - by) / (1.0 + std::fabs(rep.pobj) + std::fabs(by));
+      rep.lambda_min = lo.lo[0];
+      rep.lambda_max = lo.hi;
+      rep.sigma = sigma;
+      rep.outer = k + 1;
+      rep.p = p;
+      const double eta = std::max(rep.eta_p, std::max(rep.eta_d, rep.eta_g));
+      if (P.verbose)
+        std::fprintf(stderr,
+                     "[manidsdp] k=%d p=%d sigma=%.3g rtr=%d gnorm=%.3e eta=(%.2e %.2e %.2e) "
+                     "lmin=%.3e V=%.12f hv=%d lz=%d\n",
+                     k, p, sigma, ro.iters, ro.gnorm, rep.eta_p, rep.eta_d, rep.eta_g, lo.lo[0], by,
+                     c->hessvecs, lo.steps);
+      if (!std::isfinite(eta)) {
+        status = MANIDSDP_E_NONFINITE;
+        break;
+      }
+      if (eta <= P.tol) {
+        status = MANIDSDP_OK;
+        break;
+      }
+      // step 10 (first half): drop numerically null directions of Y
+      {
+        launch_gram<double>(N, p, p, c->Y, c->Y, c->M2, c->s);
+        std::vector<double> A(size_t(p) * p);
+        MDS_CUDA(cudaMemcpyAsync(A.data(), c->M2, A.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+        sync(c);
+        HostEig e = jacobi_eig(A, p);
+        const double wmax = e.w[p - 1];
+        std::vector<int> keep;
+        for (int i = 0; i < p; ++i)
+          if (e.w[i] > P.rank_tol * wmax || i >= p - P.p_min) keep.push_back(i);
+        const int r = int(keep.size());
+        if (r < p) {
+          std::vector<double> W(size_t(p) * r);  // row-major p x r
+          for (int i = 0; i < p; ++i)
+            for (int j = 0; j < r; ++j) W[size_t(i) * r + j] = e.V[i + size_t(p) * keep[j]];
+          MDS_CUDA(cudaMemcpyAsync(c->M1, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+          launch_gemm<double>(N, r, p, c->Y, p, c->M1, r, c->tmp, r, 1.0, 0.0, nullptr, nullptr,
+                              0.0, nullptr, c->gws, c->gws_bytes, c->s);
+          launch_retract(N, r, c->tmp, c->tmp, 0.0, c->Y, c->s);
+          p = r;
+        }
+      }
+      // step 11: sigma rule (5.1)
+      const double lhs = rnorm / (1.0 + c->normb);
+      rscale = lhs;
+      if (lhs < P.kappa1 * ro.gnorm)
+        sigma = std::max(sigma / P.gamma, P.sigma_min);
+      else if (lhs > P.kappa2 * ro.gnorm)
+        sigma = std::min(P.gamma * sigma, P.sigma_max);
+      // steps 9-10 (second half): negative curvature -> U = [0, V], Y = [Y, 0]
+      const double thr = -P.neg_tol * (1.0 + std::fabs(lo.hi));
+      int nneg = 0;
+      while (nneg < int(lo.lo.size()) && lo.lo[nneg] < thr) ++nneg;
+      const int delta = std::min(std::min(nneg, P.delta_max), P.p_max - p);
+      if (delta > 0) {
+        relayout(c, c->Y, p, p + delta);
+        MDS_CUDA(cudaMemsetAsync(c->U, 0, size_t(N) * (p + delta) * sizeof(double), c->s));
+        // Vn is N x nvec row-major; take its first delta columns
+        launch_pad_cols(N, lo.nvec, delta, c->Vn, c->Tm, c->s);
+        launch_set_cols(N, p + delta, p, delta, c->Tm, c->U, c->s);
+        p += delta;
+        have_U = true;
+        U_cols = delta;
+      }
+    }
+    c->sigma = sigma;
+    rep.rtr_iters = c->rtr_iters;
+    rep.hessvecs = c->hessvecs;
+    rep.lanczos_matvecs = c->lanczos_mv;
+    rep.status = status;
+    if (Y_out) MDS_CUDA(cudaMemcpyAsync(Y_out, c->Y, size_t(N) * rep.p * sizeof(double), cudaMemcpyDefault, c->s));
+    if (p_out) *p_out = rep.p;
+    if (y_out) MDS_CUDA(cudaMemcpyAsync(y_out, c->y, c->m * sizeof(double), cudaMemcpyDefault, c->s));
+    if (z_out) MDS_CUDA(cudaMemcpyAsync(z_out, c->z, N * sizeof(double), cudaMemcpyDefault, c->s));
+    if (Xt_out) {
+      launch_xd_from_xt(size_t(N) * N, 1, c->XD, c->idx, c->bm, c->Gt, c->s);
+      MDS_CUDA(cudaMemcpyAsync(Xt_out, c->Gt, size_t(N) * N * sizeof(double), cudaMemcpyDefault, c->s));
+    }
+    sync(c);
+    c->eval_ok = false;
+    return MANIDSDP_OK;
+  });
+  if (report) *report = rep;
+  if (gst != MANIDSDP_OK) return gst;
+  return status;
+}

@@ -1,0 +1,117 @@
+// Internal declarations shared by the CUDA translation units of libmanidsdp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/manidsdp.h"
+
+namespace mds {
+
+// Entries of the per-class inverse map pack (row, col) as (row << 16) | col,
+// so N must stay below 65536.
+constexpr int kMaxN = 65535;
+// A class's entries are processed in pieces of at most this many entries.
+constexpr int kPieceLen = 32;
+// Threads of the reduction kernels; the partial-sum buffers hold kRedBlocks values.
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+
+struct DeviceError {
+  cudaError_t err;
+};
+
+#define MDS_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) throw ::mds::DeviceError{e_}; \
+  } while (0)
+
+// ---- the per-class inverse map (built on the host at setup) -----------------
+struct ClassMap {
+  int32_t n_entries = 0;  // entries (b <= g), grouped by class
+  int32_t n_pieces = 0;
+  int32_t n_multi = 0;    // classes split into more than one piece
+  uint32_t* ent = nullptr;        // [n_entries] (b << 16) | g
+  int32_t* piece_start = nullptr; // [n_pieces + 1]
+  int32_t* piece_class = nullptr; // [n_pieces]
+  int32_t* multi_class = nullptr; // [n_multi] classes with > 1 piece
+  int32_t* multi_range = nullptr; // [2 n_multi] first piece and end piece of each such class
+};
+
+// ---- kernel launchers (defined in kernels_*.cu) ----------------------------
+// Segmented per-class sums over the inverse map:
+//   mode 0: out[a] = (sum_{(b,g) in a} wt * (Y_b . Y_g + C_bg)) / mult[a]     -> y(S)
+//   mode 1: out[a] = (sum_{(b,g) in a} wt * (Y_b . U_g + U_b . Y_g)) / mult[a] -> w
+// wt = 2 off the diagonal, 1 on it.  piece_buf holds one partial per piece.
+template <typename T>
+void launch_class_means(const ClassMap& cm, int N, int p, int mode, const T* Y, const T* U,
+                        const double* C, const double* mult, T* piece_buf, T* out, cudaStream_t s);
+
+// G-pass over all N x N entries (FP64):
+//   s = Y_b . Y_g, a = idx[b,g], r = y[a] - s - C_bg
+//   mode 0 (evaluate):  G = XD - sigma r ; optionally Gf = float(G);
+//                       partials: sum r^2, sum XD*s
+//   mode 1 (multiplier): XD <- XD - sigma r ; partials: sum r^2, sum XD_new*s
+// part holds 2 partial sums per block; out2 receives (sum r^2, sum XD*s) summed in a
+// fixed order.
+void launch_gpass(int N, int p, int mode, const double* Y, const int32_t* idx, const double* y,
+                  const double* C, double sigma, double* XD, double* G, float* Gf, double* part,
+                  double* out2, cudaStream_t s);
+size_t gpass_partials(int N);
+
+// out[M x ncol] = alpha * A[M x K] B[K x ncol] + beta * out, row-major with leading dims.
+// With idx/w non-null ("gather" mode) the product also adds
+//   alpha * sum_g (gscale * w[idx[b, g]]) * B2[g, :]
+// i.e. the moment matrix A*(w) applied to B2 (K must equal M = N then).
+template <typename T>
+void launch_gemm(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb, T* out, int ldc,
+                 T alpha, T beta, const int32_t* idx, const T* w, T gscale, const T* B2,
+                 void* ws, size_t ws_bytes, cudaStream_t s);
+
+// out[p1 x p2] = A[N x p1]' B[N x p2]  (deterministic: one block per output tile,
+// a fixed reduction order over N).
+template <typename T>
+void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, cudaStream_t s);
+
+// Row-local epilogue of the Hessian (Eq. (4.7)) on T = G U - sigma A*(w) Y:
+//   Ht = 2 T + 2 sigma (Y M1 + U M2)   (M1 = U'Y, M2 = Y'Y already folded into YM)
+//   HU = Ht - (Ht . Y_b) Y_b - 2 z_b U_b
+template <typename T>
+void launch_hess_epilogue(int N, int p, const T* Tm, const T* YM, const T* Y, const T* U,
+                          const double* z, double sigma, double* HU, cudaStream_t s);
+
+// Row-local ops (FP64)
+void launch_proj_tangent(int N, int p, const double* Y, const double* U, double* out, cudaStream_t s);
+void launch_retract(int N, int p, const double* Y, const double* E, double t, double* out,
+                    cudaStream_t s);  // rows of Y + t E normalised
+void launch_rowdot(int N, int p, const double* A, const double* B, double* out, cudaStream_t s);
+// grad = 2 (GY - z o Y)
+void launch_grad_from_gy(int N, int p, const double* GY, const double* z, const double* Y,
+                         double* grad, cudaStream_t s);
+void launch_to_float(size_t n, const double* a, float* out, cudaStream_t s);
+void launch_to_double(size_t n, const float* a, double* out, cudaStream_t s);
+// out = a*x + b*y (elementwise, n)
+void launch_axpby(size_t n, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s);
+// Deterministic dot products: up to 3 pairs at once. part: 3 * kRedBlocks doubles.
+void launch_dots(size_t n, int npairs, const double* const* xs, const double* const* ys,
+                 double* part, cudaStream_t s);
+// XD = Xt + b/mult at idx (D's values) (mode 0) or Xt = XD - D (mode 1)
+void launch_xd_from_xt(size_t NN, int mode, const double* in, const int32_t* idx, const double* bm,
+                       double* out, cudaStream_t s);
+// Lanczos helpers
+void launch_gemv_cert(int N, const double* XD, const double* z, const double* v, double* w,
+                      cudaStream_t s);  // w = XD v - z o v
+void launch_basis_dots(int N, int k, const double* V, const double* w, double* h, cudaStream_t s);
+void launch_basis_update(int N, int k, const double* V, const double* h, double* w, cudaStream_t s);
+// Copy N x p_old into N x p_new (zero-padding new columns) or select columns via a p_old x p_new
+// matrix (out = A W) - via launch_gemm.
+void launch_pad_cols(int N, int p_old, int p_new, const double* in, double* out, cudaStream_t s);
+void launch_set_cols(int N, int p, int c0, int nc, const double* src /*N x nc*/, double* out,
+                     cudaStream_t s);
+
+}  // namespace mds

@@ -1,0 +1,71 @@
+"""C ABI checks that need no GPU: the shared library loads and exports every
+function declared in include/manidsdp.h; the host helpers that build the BQP
+moment data agree bit for bit with the oracle (Section 3.1); argument checks
+reject malformed index maps before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2512_04406_gb300 as mds
+from oracle import moment
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(manidsdp_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(mds.lib_path())
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_params_match_documented_readings():
+    p = mds.manidsdp_default_params()
+    assert (p.sigma0, p.sigma_min, p.sigma_max, p.gamma, p.kappa1, p.kappa2) == (1.0, 1e-3, 1e6, 2.0, 0.1, 10.0)
+    assert p.tol == 1e-8 and p.p0 == 2 and p.p_min == 2 and p.delta_max == 8
+    assert mds.manidsdp_strerror(-1) == "invalid argument"
+
+
+@pytest.mark.parametrize("q,order", [(1, 2), (2, 2), (3, 2), (5, 2), (9, 2), (20, 2), (4, 1), (17, 1)])
+def test_bqp_index_map_bit_exact_vs_oracle(q, order):
+    N, m, idx = mds.manidsdp_bqp_index_map(q, order)
+    ref = moment.index_map(q, order)
+    assert (N, m) == (ref.shape[0], moment.num_monomials(q, order))
+    assert np.array_equal(idx, ref)
+
+
+@pytest.mark.parametrize("q,order", [(6, 2), (11, 2), (8, 1)])
+def test_bqp_rhs_bit_exact_vs_oracle(q, order):
+    rng = np.random.default_rng(q)
+    Q = rng.standard_normal((q, q)); Q = Q + Q.T
+    c = rng.standard_normal(q)
+    b = mds.manidsdp_bqp_rhs(q, Q, c, order)
+    ref = moment.rhs(q, Q, c, order)
+    assert np.array_equal(b, ref)
+
+
+def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
+    N, m, idx = mds.manidsdp_bqp_index_map(3, 2)
+    b = np.zeros(m)
+    bad = idx.copy(); bad[0, 1] = (bad[0, 1] + 1) % m  # breaks symmetry
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_setup(N, m, bad, b)
+    assert e.value.status == mds.E_ARG
+    bad = idx.copy(); bad[0, 0] = m  # out of range
+    with pytest.raises(mds.ManidsdpError):
+        mds.manidsdp_setup(N, m, bad, b)
+    with pytest.raises(mds.ManidsdpError):  # a class with no entry: A A* singular
+        mds.manidsdp_setup(N, m + 1, idx, np.zeros(m + 1))
