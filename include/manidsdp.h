@@ -98,6 +98,10 @@ typedef struct {
 /* Fill *params with the library defaults (the readings listed above). */
 void manidsdp_default_params(manidsdp_params* params);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * contexts).  Lets a caller count the device work inside a timed region. */
+long long manidsdp_launch_count(void);
+
 /* Human-readable text for a status code (static storage). */
 const char* manidsdp_strerror(int status);
 
@@ -178,8 +182,8 @@ int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t whic
  * N x p0 FP64, rows normalised by the library) to eta_max <= params.tol or
  * params.max_outer outer iterations.
  * Outputs (host or device; each may be NULL):
- *   Y_out  N x p_cap FP64 with p_cap = params.p_max; the first *p_out columns hold
- *          the final factor;
+ *   Y_out  capacity N x params.p_max FP64; receives the final N x (*p_out) factor
+ *          row-major with leading dimension *p_out;
  *   y_out  m FP64 (y at the final S);   z_out N FP64;
  *   Xt_out N x N FP64 final multiplier; report: host struct.
  * Returns MANIDSDP_OK when eta_max <= tol, MANIDSDP_E_NOCONV otherwise.

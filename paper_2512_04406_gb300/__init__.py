@@ -21,7 +21,7 @@ __all__ = [
     "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_subproblem_eval",
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
-    "lib_path",
+    "lib_path", "manidsdp_launch_count",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -75,6 +75,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _sig = {
     "manidsdp_default_params": (None, [ctypes.POINTER(Params)]),
     "manidsdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "manidsdp_launch_count": (ctypes.c_longlong, []),
     "manidsdp_setup": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.c_int32, ctypes.c_int64, _P,
                                       _P, ctypes.c_int32, _P, ctypes.POINTER(Params), _P]),
     "manidsdp_destroy": (None, [Context]),
@@ -136,6 +137,10 @@ def manidsdp_default_params() -> Params:
     p = Params()
     _lib.manidsdp_default_params(ctypes.byref(p))
     return p
+
+
+def manidsdp_launch_count() -> int:
+    return int(_lib.manidsdp_launch_count())
 
 
 def manidsdp_strerror(status: int) -> str:

@@ -14,6 +14,12 @@
 
 using namespace mds;
 
+#include <atomic>
+namespace mds {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace mds
+
 namespace {
 
 struct HostEig {  // eigenpairs of a small symmetric matrix, ascending
@@ -453,6 +459,8 @@ void set_state(manidsdp_ctx* c, const double* Xt_dev, double sigma) {
 
 // ============================== C ABI ========================================
 extern "C" {
+
+long long manidsdp_launch_count(void) { return mds::g_launches.load(); }
 
 void manidsdp_default_params(manidsdp_params* params) {
   if (params) default_params(params);

@@ -42,6 +42,9 @@ struct ClassMap {
   int32_t* multi_range = nullptr; // [2 n_multi] first piece and end piece of each such class
 };
 
+// Count of kernel launches issued by this library (all contexts, all threads).
+void count_launches(long long n);
+
 // ---- kernel launchers (defined in kernels_*.cu) ----------------------------
 // Segmented per-class sums over the inverse map:
 //   mode 0: out[a] = (sum_{(b,g) in a} wt * (Y_b . Y_g + C_bg)) / mult[a]     -> y(S)

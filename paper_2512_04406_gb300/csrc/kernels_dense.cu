@@ -120,6 +120,7 @@ static void gemm_cfg(int M, int ncol, int K, const T* A, int lda, const T* B, in
   T* part = static_cast<T*>(ws);
   dim3 grid(gx, gy, splits);
   constexpr int NT = (BM / TM) * (BN / TN);
+  count_launches(2);
   if (idx != nullptr)
     gemm_kernel<T, BM, BN, TM, TN, true><<<grid, NT, 0, s>>>(M, ncol, K, kchunk, A, lda, B, ldb,
                                                              idx, w, gscale, B2, part);
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(256) gram_kernel(int N, int p1, int p2, const 
 template <typename T>
 void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, cudaStream_t s) {
   dim3 grid((p2 + 15) / 16, (p1 + 15) / 16);
+  count_launches(1);
   gram_kernel<T><<<grid, 256, 0, s>>>(N, p1, p2, A, B, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -219,6 +221,7 @@ template <typename T>
 void launch_hess_epilogue(int N, int p, const T* Tm, const T* YM, const T* Y, const T* U,
                           const double* z, double sigma, double* HU, cudaStream_t s) {
   const int blocks = (N * 32 + 255) / 256;
+  count_launches(1);
   hess_epilogue_kernel<T><<<blocks, 256, 0, s>>>(N, p, Tm, YM, Y, U, z, sigma, HU);
   MDS_CUDA(cudaGetLastError());
 }
@@ -261,15 +264,18 @@ __global__ void rowop_kernel(int N, int p, const double* __restrict__ Y,
 
 void launch_proj_tangent(int N, int p, const double* Y, const double* U, double* out,
                          cudaStream_t s) {
+  count_launches(1);
   rowop_kernel<0><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, Y, U, 0.0, out);
   MDS_CUDA(cudaGetLastError());
 }
 void launch_retract(int N, int p, const double* Y, const double* E, double t, double* out,
                     cudaStream_t s) {
+  count_launches(1);
   rowop_kernel<1><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, Y, E, t, out);
   MDS_CUDA(cudaGetLastError());
 }
 void launch_rowdot(int N, int p, const double* A, const double* B, double* out, cudaStream_t s) {
+  count_launches(1);
   rowop_kernel<2><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, B, A, 0.0, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -287,6 +293,7 @@ void launch_grad_from_gy(int N, int p, const double* GY, const double* z, const 
   const size_t n = size_t(N) * p;
   int b = int((n + 255) / 256);
   if (b > 8192) b = 8192;
+  count_launches(1);
   grad_kernel<<<b, 256, 0, s>>>(N, p, GY, z, Y, grad);
   MDS_CUDA(cudaGetLastError());
 }
@@ -306,10 +313,12 @@ static int grid_for(size_t n) {
   return int(b > 8192 ? 8192 : (b == 0 ? 1 : b));
 }
 void launch_to_float(size_t n, const double* a, float* out, cudaStream_t s) {
+  count_launches(1);
   to_float_kernel<<<grid_for(n), 256, 0, s>>>(n, a, out);
   MDS_CUDA(cudaGetLastError());
 }
 void launch_to_double(size_t n, const float* a, double* out, cudaStream_t s) {
+  count_launches(1);
   to_double_kernel<<<grid_for(n), 256, 0, s>>>(n, a, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -322,6 +331,7 @@ __global__ void axpby_kernel(size_t n, double a, const double* __restrict__ x, d
 }
 void launch_axpby(size_t n, double a, const double* x, double b, const double* y, double* out,
                   cudaStream_t s) {
+  count_launches(1);
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, a, x, b, y, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -379,7 +389,9 @@ void launch_dots(size_t n, int npairs, const double* const* xs, const double* co
   }
   size_t nbz = (n + kRedThreads - 1) / kRedThreads;
   const int nb = int(nbz < size_t(kRedBlocks) ? (nbz == 0 ? 1 : nbz) : kRedBlocks);
+  count_launches(1);
   dots_kernel<<<nb, kRedThreads, 0, s>>>(n, npairs, a, part);
+  count_launches(1);
   dots_final_kernel<<<1, kRedThreads, 0, s>>>(npairs, nb, part, part + 3 * kRedBlocks);
   MDS_CUDA(cudaGetLastError());
 }
@@ -394,6 +406,7 @@ __global__ void xd_kernel(size_t NN, int mode, const double* __restrict__ in,
 }
 void launch_xd_from_xt(size_t NN, int mode, const double* in, const int32_t* idx, const double* bm,
                        double* out, cudaStream_t s) {
+  count_launches(1);
   xd_kernel<<<grid_for(NN), 256, 0, s>>>(NN, mode, in, idx, bm, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -413,6 +426,7 @@ __global__ void gemv_cert_kernel(int N, const double* __restrict__ XD,
 }
 void launch_gemv_cert(int N, const double* XD, const double* z, const double* v, double* w,
                       cudaStream_t s) {
+  count_launches(1);
   gemv_cert_kernel<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, XD, z, v, w);
   MDS_CUDA(cudaGetLastError());
 }
@@ -436,6 +450,7 @@ __global__ void __launch_bounds__(256) basis_dots_kernel(int N, const double* __
 void launch_basis_dots(int N, int k, const double* V, const double* w, double* h,
                        cudaStream_t s) {
   if (k <= 0) return;
+  count_launches(1);
   basis_dots_kernel<<<k, 256, 0, s>>>(N, V, w, h);
   MDS_CUDA(cudaGetLastError());
 }
@@ -451,6 +466,7 @@ __global__ void basis_update_kernel(int N, int k, const double* __restrict__ V,
 void launch_basis_update(int N, int k, const double* V, const double* h, double* w,
                          cudaStream_t s) {
   if (k <= 0) return;
+  count_launches(1);
   basis_update_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, k, V, h, w);
   MDS_CUDA(cudaGetLastError());
 }
@@ -465,6 +481,7 @@ __global__ void pad_cols_kernel(int N, int p_old, int p_new, const double* __res
   }
 }
 void launch_pad_cols(int N, int p_old, int p_new, const double* in, double* out, cudaStream_t s) {
+  count_launches(1);
   pad_cols_kernel<<<grid_for(size_t(N) * p_new), 256, 0, s>>>(N, p_old, p_new, in, out);
   MDS_CUDA(cudaGetLastError());
 }
@@ -479,6 +496,7 @@ __global__ void set_cols_kernel(int N, int p, int c0, int nc, const double* __re
 }
 void launch_set_cols(int N, int p, int c0, int nc, const double* src, double* out,
                      cudaStream_t s) {
+  count_launches(1);
   set_cols_kernel<<<grid_for(size_t(N) * nc), 256, 0, s>>>(N, p, c0, nc, src, out);
   MDS_CUDA(cudaGetLastError());
 }

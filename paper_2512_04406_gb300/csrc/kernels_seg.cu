@@ -76,6 +76,7 @@ static void dispatch_means(const ClassMap& cm, int N, int p, int mode, const T* 
   const long long lanes = (long long)cm.n_pieces * LG;
   const int blocks = int((lanes + threads - 1) / threads);
   if (blocks > 0) {
+    count_launches(1);
     if (mode == 0)
       class_means_kernel<T, LG, 0><<<blocks, threads, 0, s>>>(cm.n_pieces, N, p, cm.ent,
                                                               cm.piece_start, cm.piece_class, Y,
@@ -85,6 +86,7 @@ static void dispatch_means(const ClassMap& cm, int N, int p, int mode, const T* 
                                                               cm.piece_start, cm.piece_class, Y,
                                                               U, C, mult, piece_buf, out);
   }
+  if (cm.n_multi > 0) count_launches(1);
   if (cm.n_multi > 0)
     class_finalize_kernel<T><<<(cm.n_multi + 255) / 256, 256, 0, s>>>(
         cm.n_multi, cm.multi_class, cm.multi_range, piece_buf, mult, out);
@@ -241,6 +243,7 @@ void launch_gpass(int N, int p, int mode, const double* Y, const int32_t* idx, c
                   double* out2, cudaStream_t s) {
   const int nt = (N + GP_TILE - 1) / GP_TILE;
   dim3 grid(nt, nt);
+  count_launches(2);
   if (mode == 0)
     gpass_kernel<0><<<grid, 256, 0, s>>>(N, p, Y, idx, y, C, sigma, XD, G, Gf, part);
   else
