@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""ManiDSDP on one GB300: solve time to KKT residual <= 1e-8.
+
+Workload: the order-2 moment relaxation of a dense binary quadratic program
+min x'Qx + c'x over x in {-1,1}^80 (Section 6.1): moment matrix 3241 x 3241,
+1,666,981 classes (monomials of degree <= 4), Q and c iid N(0,1) from seed 0,
+p_0 = ceil(ln m) = 15 (Section 6.1 sets p_0 = ceil(log m)).
+
+A step is one full solve (Algorithm 1: every RTR iteration, Hessian-vector
+product, multiplier update and Lanczos run) from the seeded start to
+eta_max <= 1e-8 with the mixed-precision form (FP32 Hessian-vector products,
+FP64 cost, gradient, multiplier, KKT residuals and Lanczos).  Inputs sit in HBM
+before the timed region; the working set (index map 42 MB, three N x N FP64
+matrices 252 MB) exceeds the 129 MB L2, so no flush is needed between steps.
+
+Under torchrun (N > 1) each rank solves its own replica (the single-instance
+path has no exchange step on one GPU); value = total solves / max-over-ranks time.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload and projects the full-solve time from the GPU
+solve's operation counts (see the JSON's cpu_baseline.sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "solve time to KKT<=1e-8 (dense BQP order-2 relaxation, q=80)"
+UNIT = "s/solve"
+
+# Operation counts of one mixed-precision solve of this workload, used to scale
+# the sampled oracle timings to a full solve when no GPU run precedes them.
+# bench.py overwrites them with the counts of its own GPU solve when it has one.
+DEFAULT_COUNTS = dict(hessvecs=3000, evals=600, grads=450, lanczos_matvecs=6000, p=16)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--q", type=int, default=80)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--hv-reps", type=int, default=30)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def workload(q, seed):
+    import paper_2512_04406_gb300 as mds
+    from synthetic import bqp_instance
+    Q, c = bqp_instance(q, seed)
+    N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
+    b = mds.manidsdp_bqp_rhs(q, Q, c, 2)
+    p0 = int(math.ceil(math.log(m)))
+    return Q, c, N, m, idx, b, p0
+
+
+def hessvec_bytes(N, m, n_entries, n_pieces, p, fp_bytes):
+    """Algorithmic DRAM bytes of one Hessian-vector product (Proposition 4.2):
+    class-mean pass reads the inverse map (4 B per upper-triangle entry) and the
+    piece table (8 B per piece) and writes w (fp_bytes per class); the gather-GEMM
+    pass reads G (fp_bytes per entry) and the index map (4 B per entry); the
+    N x p operands Y, U are read and HU written once (8 B each in FP64 I/O)."""
+    return (4 * n_entries + 8 * n_pieces + fp_bytes * m + (fp_bytes + 4) * N * N
+            + 3 * 8 * N * p)
+
+
+def measure_hessvec(mds, torch, ctx, N, p, reps, precision, seed=11):
+    """Mean device time of one Hessian-vector product at a random unit-row Y
+    (CUDA events on the library's stream, params.profile path)."""
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((N, p)); Y /= np.linalg.norm(Y, axis=1)[:, None]
+    U = rng.standard_normal((N, p))
+    Yd = torch.tensor(Y, device="cuda"); Ud = torch.tensor(U, device="cuda")
+    HU = torch.empty_like(Yd)
+    mds.manidsdp_set_state(ctx, None, 1.0)
+    mds.manidsdp_subproblem_eval(ctx, Yd, p)
+    for _ in range(3):
+        mds.manidsdp_hessvec(ctx, Yd, Ud, p, HU, precision)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        mds.manidsdp_hessvec(ctx, Yd, Ud, p, HU, precision)
+        e1.record(s)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def cpu_baseline(q, seed, counts, budget_s):
+    """The FP64 oracle, as it stands, on this host: time its Hessian-vector
+    product, cost-plus-gradient evaluation and certificate matvec at the
+    workload's size, then scale by the GPU solve's operation counts."""
+    from oracle import manidsdp as om, moment, operators as ops, subproblem as sp
+    from synthetic import bqp_instance, gaussian_factor
+    t_setup = time.perf_counter()
+    Q, c = bqp_instance(q, seed)
+    idx = moment.index_map(q)
+    m = moment.num_monomials(q)
+    prob = om.make_problem(idx, moment.multiplicities(idx, m), moment.rhs(q, Q, c))
+    t_setup = time.perf_counter() - t_setup
+    N = idx.shape[0]
+    p = max(2, int(round(counts["p"])))
+    Y = gaussian_factor(N, p, seed)
+    Y /= np.linalg.norm(Y, axis=1)[:, None]
+    Xt = np.zeros((N, N))
+    U = sp.proj_tangent(Y, np.random.default_rng(1).standard_normal((N, p)))
+    deadline = time.perf_counter() + budget_s
+    t_hv, t_ev, t_mv = [], [], []
+    G = sp.egrad_S(Y, prob, Xt, 1.0)
+    X = Xt + prob["D"] - np.diag(sp.rowdot(G @ Y, Y))
+    v = np.ones(N) / math.sqrt(N)
+    while time.perf_counter() < deadline or not t_hv:
+        t0 = time.perf_counter(); sp.rhess(Y, U, prob, Xt, 1.0, G); t_hv.append(time.perf_counter() - t0)
+        t0 = time.perf_counter(); sp.cost(Y, prob, Xt, 1.0); sp.rgrad(Y, prob, Xt, 1.0)
+        t_ev.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        for _ in range(10):
+            v = X @ v; v /= np.linalg.norm(v)
+        t_mv.append((time.perf_counter() - t0) / 10)
+    hv, ev, mv = statistics.median(t_hv), statistics.median(t_ev), statistics.median(t_mv)
+    proj = hv * counts["hessvecs"] + ev * counts["evals"] + mv * counts["lanczos_matvecs"]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {
+        "value": proj, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": (f"oracle FP64 at q={q} (N={N}, m={m}, p={p}): {len(t_hv)} Hessian-vector products "
+                   f"({hv:.3f} s each), {len(t_ev)} cost+gradient evaluations ({ev:.3f} s), "
+                   f"{10 * len(t_mv)} certificate matvecs ({mv * 1e3:.1f} ms); value projects a full "
+                   f"solve from the GPU solve's counts (hessvecs={counts['hessvecs']}, "
+                   f"evals={counts['evals']}, lanczos matvecs={counts['lanczos_matvecs']}); "
+                   f"index-map setup {t_setup:.1f} s not included"),
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    cb = None
+    budget = max(2.0, min(args.cpu_sample_s, 60.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.q, args.seed, DEFAULT_COUNTS, budget)
+        if i >= args.warmup:
+            steps.append(cb["value"])
+    value = statistics.mean(steps)
+    cb["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1) Q, c)",
+        "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
+                   "N": 1 + args.q + args.q * (args.q - 1) // 2},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2512_04406_gb300 as mds
+    from synthetic import gaussian_factor
+
+    rank, world, local = dist_env()
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = mds.PREC_MIXED if args.precision == "mixed" else mds.PREC_FP64
+    Q, c, N, m, idx, b, p0 = workload(args.q, args.seed)
+    prm = mds.manidsdp_default_params()
+    prm.precision_mode = prec
+    prm.p_max = 256
+    prm.profile = 1
+    stream = torch.cuda.current_stream()
+    ctx = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
+    Y0 = torch.tensor(gaussian_factor(N, p0, args.seed + rank), device="cuda")
+    for _ in range(args.warmup):
+        mds.manidsdp_solve(ctx, Y0, p0)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = mds.manidsdp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    reps = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        rep, p_fin = mds.manidsdp_solve(ctx, Y0, p0)
+        reps.append(rep)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = mds.manidsdp_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop()
+    rep = reps[-1]
+    ok = all(r.status == mds.OK and r.eta_max <= 1e-8 for r in reps)
+    value = ms / 1e3 / (args.steps * world)
+
+    # dominant kernel: the Hessian-vector product, live (phase events inside the
+    # timed solves) and in isolation at p = p_0
+    hv_ms_live = rep.ms_hessvec / max(1, rep.hessvecs)
+    p_avg = rep.hessvec_p_sum / max(1, rep.hessvecs)
+    fp_bytes = 4 if prec == mds.PREC_MIXED else 8
+    n_entries = N * (N + 1) // 2
+    n_pieces = m + 2 * (args.q - 1) * 2 + (N + 31) // 32  # classes + extra pieces of long classes
+    bytes_live = hessvec_bytes(N, m, n_entries, n_pieces, p_avg, fp_bytes)
+    flops_live = 6.0 * N * N * p_avg
+    hv_ms_iso = measure_hessvec(mds, torch, ctx, N, p0, args.hv_reps, prec)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if prec == mds.PREC_MIXED:
+        roof = {"bound": "hbm", "achieved": bytes_live / (hv_ms_live * 1e-3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "traffic": None, "peak_source": peak_src,
+                "kernel": "Hessian-vector product (FP32 class means + gather GEMM + epilogue)",
+                "avg_ms": hv_ms_live, "p_avg": p_avg,
+                "isolated_ms_at_p0": hv_ms_iso,
+                "isolated_gbs_at_p0": hessvec_bytes(N, m, n_entries, n_pieces, p0, 4) / (hv_ms_iso * 1e-3) / 1e9,
+                "alu_tflops": flops_live / (hv_ms_live * 1e-3) / 1e12}
+    else:
+        fp64_peak = 1.19  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x ~1.95 GHz, probe-measured
+        roof = {"bound": "alu", "achieved": flops_live / (hv_ms_live * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "traffic": None, "peak_source": "FP64 FMA probe on GB300",
+                "kernel": "Hessian-vector product (FP64)", "avg_ms": hv_ms_live, "p_avg": p_avg}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    e2e = None
+    if not args.no_e2e:
+        # the user's call: host index map and b, host start, host outputs
+        y_host = np.empty(m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2 = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
+        Y0h = gaussian_factor(N, p0, args.seed + rank)
+        Yout = np.empty(N * prm.p_max)
+        rep2, p2 = mds.manidsdp_solve(ctx2, Y0h, p0, Y_out=Yout, y_out=y_host)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        mds.manidsdp_destroy(ctx2)
+        e2e = {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(idx.nbytes + b.nbytes + Y0h.nbytes),
+               "d2h_bytes_per_step": int(y_host.nbytes + N * p2 * 8),
+               "includes": "setup (index-map validation, inverse map, H2D) + solve + D2H of y and Y"}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = dict(hessvecs=rep.hessvecs, evals=rep.evals, grads=rep.grads,
+                      lanczos_matvecs=rep.lanczos_matvecs, p=p_avg)
+        cb = cpu_baseline(args.q, args.seed, counts, args.cpu_sample_s)
+
+    mds.manidsdp_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64 (FP32 Hessian-vector products, FP64 elsewhere)" if prec == mds.PREC_MIXED else "f64",
+            "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
+            "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
+                       "N": N, "m": m, "p0": p0, "precision": args.precision,
+                       "l2": "working set > L2 (idx 42 MB + 3 x 84 MB N x N FP64), no flush",
+                       "parallelism": f"replicas{world}"},
+            "converged": ok, "eta_max": rep.eta_max, "value_bound": rep.value, "outer": rep.outer,
+            "rtr_iters": rep.rtr_iters, "hessvecs": rep.hessvecs, "p_final": rep.p,
+            "phase_ms": {"hessvec": rep.ms_hessvec, "eval": rep.ms_eval, "grad": rep.ms_grad,
+                         "lanczos_wall": rep.ms_lanczos},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -82,7 +82,8 @@ typedef struct {
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */
   int32_t precision_mode; /* MANIDSDP_PREC_* */
   int32_t verbose;        /* 1: one line per outer iteration on stderr */
-  int32_t reserved;
+  int32_t profile;        /* 1: time each phase with CUDA events on the context's
+                             stream (fills the ms_* fields of the report) */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */
@@ -91,8 +92,13 @@ typedef struct {
   double value;               /* b'y: the relaxation value (dual objective) */
   double pobj;                /* <C, X + Diag z> + sum(z) */
   double lambda_min, lambda_max, sigma;
+  /* device time per phase, summed over the solve (params.profile = 1, else 0):
+   * Hessian-vector products, subproblem evaluations (y, G, Psi), gradients
+   * (G Y, z, grad), Lanczos runs */
+  double ms_hessvec, ms_eval, ms_grad, ms_lanczos;
+  double hessvec_p_sum;       /* sum of p over the Hessian-vector products */
   int32_t outer, rtr_iters, hessvecs, p;
-  int32_t lanczos_matvecs, status, reserved0, reserved1;
+  int32_t lanczos_matvecs, status, evals, grads;
 } manidsdp_report;
 
 /* Fill *params with the library defaults (the readings listed above). */

@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
         "tol_grad_min", "tol_grad_max", "tol_grad_factor", "rank_tol", "neg_tol", "tcg_floor")] + [
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
-            "carry_halvings", "lanczos_k", "precision_mode", "verbose", "reserved")]
+            "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -53,10 +53,11 @@ class Params(ctypes.Structure):
 
 class Report(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
-        "eta_p", "eta_d", "eta_g", "value", "pobj", "lambda_min", "lambda_max", "sigma")] + [
+        "eta_p", "eta_d", "eta_g", "value", "pobj", "lambda_min", "lambda_max", "sigma",
+        "ms_hessvec", "ms_eval", "ms_grad", "ms_lanczos", "hessvec_p_sum")] + [
         (n, ctypes.c_int32) for n in (
-            "outer", "rtr_iters", "hessvecs", "p", "lanczos_matvecs", "status", "reserved0",
-            "reserved1")]
+            "outer", "rtr_iters", "hessvecs", "p", "lanczos_matvecs", "status", "evals",
+            "grads")]
 
     @property
     def eta_max(self):

@@ -5,6 +5,7 @@
 // sizes, trust-region ratio, sigma rule, rank update); every vector and matrix
 // operation runs in the kernels of kernels_seg.cu and kernels_dense.cu.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <functional>
 #include <new>
@@ -197,8 +198,11 @@ struct manidsdp_ctx {
   int eval_p = 0;
   bool eval_ok = false;
   double psi = 0.0, r2 = 0.0;
-  // counters
-  int hessvecs = 0, rtr_iters = 0, lanczos_mv = 0;
+  // counters and phase timers
+  int hessvecs = 0, rtr_iters = 0, lanczos_mv = 0, evals = 0, grads = 0;
+  double hv_psum = 0.0;
+  double ms_hv = 0.0, ms_eval = 0.0, ms_grad = 0.0, ms_lz = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
@@ -213,6 +217,19 @@ T* dalloc(manidsdp_ctx* c, size_t n) {
 }
 
 void sync(manidsdp_ctx* c) { MDS_CUDA(cudaStreamSynchronize(c->s)); }
+
+// Phase timing with CUDA events on the context's stream (params.profile).
+void tstart(manidsdp_ctx* c) {
+  if (c->prm.profile) MDS_CUDA(cudaEventRecord(c->ev0, c->s));
+}
+void tstop(manidsdp_ctx* c, double* acc) {
+  if (!c->prm.profile) return;
+  MDS_CUDA(cudaEventRecord(c->ev1, c->s));
+  MDS_CUDA(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  MDS_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  *acc += double(ms);
+}
 
 // Deterministic dot products of up to three pairs of length n; results on the host.
 void dots(manidsdp_ctx* c, size_t n, int k, const double* x0, const double* y0, double* out,
@@ -230,9 +247,12 @@ void dots(manidsdp_ctx* c, size_t n, int k, const double* x0, const double* y0, 
 // Psi, y and G (and Gf in mixed mode) at Y.
 void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, float* Gf,
               double* psi, double* r2) {
+  tstart(c);
+  c->evals++;
   launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y, c->s);
   launch_gpass(c->N, p, 0, Y, c->idx, y, c->C, c->sigma, c->XD, G, Gf, c->part, c->out2, c->s);
   MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  tstop(c, &c->ms_eval);
   sync(c);
   *r2 = c->hp[0];
   *psi = c->hp[1] + c->xdc + 0.5 * c->sigma * c->hp[0];
@@ -241,10 +261,13 @@ void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, flo
 // GY = G Y, z = diag(G S), grad = 2 (GY - Diag(z) Y); returns ||grad||.
 double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
   const int N = c->N;
+  tstart(c);
+  c->grads++;
   launch_gemm<double>(N, p, N, G, N, Y, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0, nullptr,
                       c->gws, c->gws_bytes, c->s);
   launch_rowdot(N, p, c->GY, Y, c->z, c->s);
   launch_grad_from_gy(N, p, c->GY, c->z, Y, c->grad, c->s);
+  tstop(c, &c->ms_grad);
   double gg;
   dots(c, size_t(N) * p, 1, c->grad, c->grad, &gg);
   return std::sqrt(gg);
@@ -254,6 +277,7 @@ double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
 void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* HU, int prec) {
   const int N = c->N;
   const size_t np = size_t(N) * p;
+  tstart(c);
   launch_proj_tangent(N, p, Y, U, c->Up, c->s);
   if (prec == MANIDSDP_PREC_FP64) {
     launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
@@ -285,7 +309,9 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
                        0.0f, nullptr, c->gws, c->gws_bytes, c->s);
     launch_hess_epilogue<float>(N, p, c->Tmf, c->YMf, c->Yf, c->Upf, c->z, c->sigma, HU, c->s);
   }
+  tstop(c, &c->ms_hv);
   c->hessvecs++;
+  c->hv_psum += p;
 }
 
 struct LanczosOut {
@@ -298,6 +324,12 @@ struct LanczosOut {
 // Lanczos with full reorthogonalisation on X = XD - Diag(z) (z on device).
 LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
   const int N = c->N;
+  double t_lz = 0.0;
+  if (c->prm.profile) {
+    sync(c);
+    t_lz = -1.0;
+  }
+  const auto wall0 = std::chrono::steady_clock::now();
   int k = std::min(std::min(kcap, c->kmax), N);
   if (k < 1) k = 1;
   std::vector<double> v0(N);
@@ -385,6 +417,8 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
   }
   out.nvec = ns;
   sync(c);
+  if (t_lz < 0.0)
+    c->ms_lz += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   return out;
 }
 
@@ -414,6 +448,7 @@ void default_params(manidsdp_params* p) {
   p->lanczos_k = 300;
   p->precision_mode = MANIDSDP_PREC_FP64;
   p->verbose = 0;
+  p->profile = 0;
 }
 
 struct NonFinite {};
@@ -437,6 +472,9 @@ void release(manidsdp_ctx* c) {
   c->allocs.clear();
   if (c->hp) cudaFreeHost(c->hp);
   c->hp = nullptr;
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  c->ev0 = c->ev1 = nullptr;
 }
 
 // Reset the ALM state: XD = Xt + D with Xt given (device) or zero; sigma.
@@ -544,6 +582,8 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->prm = prm;
     c->s = static_cast<cudaStream_t>(stream);
     MDS_CUDA(cudaMallocHost(&c->hp, 64 * sizeof(double)));
+    MDS_CUDA(cudaEventCreate(&c->ev0));
+    MDS_CUDA(cudaEventCreate(&c->ev1));
     c->idx = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
     c->mult = dalloc<double>(c, m);
@@ -854,7 +894,8 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
   int gst = guard([&]() -> int {
     const int N = c->N;
     const manidsdp_params& P = c->prm;
-    c->hessvecs = c->rtr_iters = c->lanczos_mv = 0;
+    c->hessvecs = c->rtr_iters = c->lanczos_mv = c->evals = c->grads = 0;
+    c->hv_psum = c->ms_hv = c->ms_eval = c->ms_grad = c->ms_lz = 0.0;
     set_state(c, nullptr, P.sigma0);
     int p = p0;
     MDS_CUDA(cudaMemcpyAsync(c->tmp, Y0, size_t(N) * p * sizeof(double), cudaMemcpyDefault, c->s));
@@ -992,6 +1033,13 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     rep.rtr_iters = c->rtr_iters;
     rep.hessvecs = c->hessvecs;
     rep.lanczos_matvecs = c->lanczos_mv;
+    rep.evals = c->evals;
+    rep.grads = c->grads;
+    rep.hessvec_p_sum = c->hv_psum;
+    rep.ms_hessvec = c->ms_hv;
+    rep.ms_eval = c->ms_eval;
+    rep.ms_grad = c->ms_grad;
+    rep.ms_lanczos = c->ms_lz;
     rep.status = status;
     if (Y_out) MDS_CUDA(cudaMemcpyAsync(Y_out, c->Y, size_t(N) * rep.p * sizeof(double), cudaMemcpyDefault, c->s));
     if (p_out) *p_out = rep.p;
