@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "solve time to KKT<=1e-8 (dense BQP order-2 relaxation, q=80)"
+METRIC = "solve time to KKT≤1e-8 (mixed vs FP64 GPU); Hess-vec GB/s or TC % of roofline"
 UNIT = "s/solve"
 
 # Operation counts of one mixed-precision solve of this workload, used to scale

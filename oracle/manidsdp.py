@@ -23,6 +23,8 @@ Readings where the paper is silent (each also listed in the design notes):
     renormalised), keeping p >= p_min; then, if lambda_min(X) < -neg_tol * (1 + |lambda_max(X)|),
     delta = min(#such eigenvalues among the delta_max smallest, delta_max) zero
     columns are appended, p <= p_max.
+  * tCG also stops once ||r_j|| <= tcg_abs * eps_k (tcg_abs = 0.1): the RTR
+    asks for ||grad|| <= eps_k, so resolving the model gradient further is wasted.
   * Use of the carried U (step 3, "supplied with"): if the exact curvature
     <U, Hess Psi_{k+1}(Yhat)[U]> (Proposition 5.1) is negative, take
     Y <- Retr(Yhat + t U) for the largest t in sqrt(N) 2^-j, j = 0..carry_halvings-1,
@@ -45,7 +47,7 @@ DEFAULTS = dict(
     sigma0=1.0, sigma_min=1e-3, sigma_max=1e6, gamma=2.0, kappa1=0.1, kappa2=10.0,
     p0=2, p_min=2, p_max=256, delta_max=8,
     max_outer=300, max_rtr=200, max_tcg=500, tol=1e-8,
-    tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1e-1, tcg_floor=1e-10,
+    tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1e-1, tcg_floor=1e-10, tcg_abs=0.1,
     rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30,
     lanczos_k=300,
 )
@@ -147,7 +149,8 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
             return sp.rhess(Yv, Uv, prob, Xt, sigma, G)
 
         Y, info = rtr(Y, f, grad, hess, sp.retract, Delta_bar, tol_k,
-                      max_iter=prm["max_rtr"], max_tcg=prm["max_tcg"], tcg_floor=prm["tcg_floor"])
+                      max_iter=prm["max_rtr"], max_tcg=prm["max_tcg"], tcg_floor=prm["tcg_floor"],
+                      tcg_abs=prm["tcg_abs"])
         totals["rtr"] += info["iters"]
         totals["hessvecs"] += info["hessvecs"]
         gnorm = info["gradnorm"]

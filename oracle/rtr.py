@@ -31,7 +31,7 @@ def inner(a, b) -> float:
     return float(np.sum(a * b))
 
 
-def tcg(x, g, hess, Delta, kappa=0.1, theta=1.0, max_iter=1000, floor=1e-10):
+def tcg(x, g, hess, Delta, kappa=0.1, theta=1.0, max_iter=1000, floor=1e-10, abs_tol=0.0):
     """Truncated CG.  Returns (eta, Heta, n_iter, stop_reason).  The relative
     residual target min(||r_0||^theta, kappa) is floored at ``floor``: below
     it the Hessian-vector products themselves are not that accurate."""
@@ -63,7 +63,7 @@ def tcg(x, g, hess, Delta, kappa=0.1, theta=1.0, max_iter=1000, floor=1e-10):
         ee = ee_new
         r = r + alpha * Hd
         rr_new = inner(r, r)
-        if math.sqrt(rr_new) <= r0 * max(min(r0 ** theta, kappa), floor):
+        if math.sqrt(rr_new) <= max(r0 * max(min(r0 ** theta, kappa), floor), abs_tol):
             stop = "converged"
             return eta, Heta, j, stop
         beta = rr_new / rr
@@ -75,7 +75,8 @@ def tcg(x, g, hess, Delta, kappa=0.1, theta=1.0, max_iter=1000, floor=1e-10):
 
 
 def rtr(x0, f, grad, hess, retr, Delta_bar, tol_grad, max_iter=200, max_tcg=1000,
-        Delta0=None, rho_prime=0.1, kappa=0.1, theta=1.0, tcg_floor=1e-10, log=None):
+        Delta0=None, rho_prime=0.1, kappa=0.1, theta=1.0, tcg_floor=1e-10, tcg_abs=0.0,
+        log=None):
     """Riemannian trust region.  ``grad`` returns the Riemannian gradient;
     ``hess(x, u)`` the Riemannian Hessian applied to a tangent vector.
     Returns (x, info)."""
@@ -88,7 +89,8 @@ def rtr(x0, f, grad, hess, retr, Delta_bar, tol_grad, max_iter=200, max_tcg=1000
     for it in range(max_iter):
         if gn <= tol_grad:
             break
-        eta, Heta, nin, stop = tcg(x, g, hess, Delta, kappa, theta, max_tcg, tcg_floor)
+        eta, Heta, nin, stop = tcg(x, g, hess, Delta, kappa, theta, max_tcg, tcg_floor,
+                                   tcg_abs * tol_grad)
         info["hessvecs"] += nin
         x_new = retr(x, eta)
         f_new = f(x_new)

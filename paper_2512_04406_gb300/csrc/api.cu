@@ -284,8 +284,8 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
                                c->s);
     launch_gemm<double>(N, p, N, c->G, N, c->Up, p, c->Tm, p, 1.0, 0.0, c->idx, c->w, -c->sigma,
                         Y, c->gws, c->gws_bytes, c->s);
-    launch_gram<double>(N, p, p, c->Up, Y, c->M1, c->s);
-    launch_gram<double>(N, p, p, Y, Y, c->M2, c->s);
+    launch_gram<double>(N, p, p, c->Up, Y, c->M1, c->gws, c->gws_bytes, c->s);
+    launch_gram<double>(N, p, p, Y, Y, c->M2, c->gws, c->gws_bytes, c->s);
     launch_gemm<double>(N, p, p, Y, p, c->M1, p, c->YM, p, 1.0, 0.0, nullptr, nullptr, 0.0,
                         nullptr, c->gws, c->gws_bytes, c->s);
     launch_gemm<double>(N, p, p, c->Up, p, c->M2, p, c->YM, p, 1.0, 1.0, nullptr, nullptr, 0.0,
@@ -301,8 +301,8 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, c->s);
     launch_gemm<float>(N, p, N, c->Gf, N, c->Upf, p, c->Tmf, p, 1.0f, 0.0f, c->idx, c->wf,
                        float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
-    launch_gram<float>(N, p, p, c->Upf, c->Yf, c->M1f, c->s);
-    launch_gram<float>(N, p, p, c->Yf, c->Yf, c->M2f, c->s);
+    launch_gram<float>(N, p, p, c->Upf, c->Yf, c->M1f, c->gws, c->gws_bytes, c->s);
+    launch_gram<float>(N, p, p, c->Yf, c->Yf, c->M2f, c->gws, c->gws_bytes, c->s);
     launch_gemm<float>(N, p, p, c->Yf, p, c->M1f, p, c->YMf, p, 1.0f, 0.0f, nullptr, nullptr,
                        0.0f, nullptr, c->gws, c->gws_bytes, c->s);
     launch_gemm<float>(N, p, p, c->Upf, p, c->M2f, p, c->YMf, p, 1.0f, 1.0f, nullptr, nullptr,
@@ -437,6 +437,7 @@ void default_params(manidsdp_params* p) {
   p->rank_tol = 1e-10;
   p->neg_tol = 1e-10;
   p->tcg_floor = 1e-10;
+  p->tcg_abs = 0.1;
   p->p0 = 2;
   p->p_min = 2;
   p->p_max = 256;
@@ -785,7 +786,7 @@ struct TcgOut {
 };
 
 // Truncated CG on the trust-region model at c->Y (gradient in c->grad).
-TcgOut tcg(manidsdp_ctx* c, int p, double Delta) {
+TcgOut tcg(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
   const int N = c->N;
   const size_t n = size_t(N) * p;
   const manidsdp_params& P = c->prm;
@@ -797,7 +798,8 @@ TcgOut tcg(manidsdp_ctx* c, int p, double Delta) {
   dots(c, n, 1, c->r, c->r, &rr);
   const double r0 = std::sqrt(rr);
   double ee = 0.0, ed = 0.0, dd = rr;
-  const double target = r0 * std::max(std::min(std::pow(r0, 1.0), 0.1), P.tcg_floor);
+  const double target = std::max(r0 * std::max(std::min(std::pow(r0, 1.0), 0.1), P.tcg_floor),
+                                 P.tcg_abs * tol_grad);
   for (int j = 1; j <= P.max_tcg; ++j) {
     hessvec(c, c->Y, c->delta, p, c->Hd, P.precision_mode);
     double kap;
@@ -846,7 +848,7 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
   int it = 0;
   for (; it < P.max_rtr; ++it) {
     if (gn <= tol_grad) break;
-    TcgOut t = tcg(c, p, Delta);
+    TcgOut t = tcg(c, p, Delta, tol_grad);
     double d2[2];
     dots(c, n, 2, c->grad, c->eta, d2, c->eta, c->Heta);
     const double model_dec = -(d2[0] + 0.5 * d2[1]);
@@ -985,7 +987,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       }
       // step 10 (first half): drop numerically null directions of Y
       {
-        launch_gram<double>(N, p, p, c->Y, c->Y, c->M2, c->s);
+        launch_gram<double>(N, p, p, c->Y, c->Y, c->M2, c->gws, c->gws_bytes, c->s);
         std::vector<double> A(size_t(p) * p);
         MDS_CUDA(cudaMemcpyAsync(A.data(), c->M2, A.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
         sync(c);

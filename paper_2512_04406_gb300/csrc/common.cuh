@@ -78,7 +78,8 @@ void launch_gemm(int M, int ncol, int K, const T* A, int lda, const T* B, int ld
 // out[p1 x p2] = A[N x p1]' B[N x p2]  (deterministic: one block per output tile,
 // a fixed reduction order over N).
 template <typename T>
-void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, cudaStream_t s);
+void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, void* ws, size_t ws_bytes,
+                 cudaStream_t s);
 
 // Row-local epilogue of the Hessian (Eq. (4.7)) on T = G U - sigma A*(w) Y:
 //   Ht = 2 T + 2 sigma (Y M1 + U M2)   (M1 = U'Y, M2 = Y'Y already folded into YM)

@@ -5,6 +5,8 @@
 //   (Eq. (4.7)), the tangent projector (Lemma 4.1), the row-normalising
 //   retraction, deterministic reductions, and the Lanczos helpers for the
 //   certificate X = Xt + D - Diag(z) (Algorithm 1, step 9).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mds {
@@ -159,40 +161,70 @@ template void launch_gemm<float>(int, int, int, const float*, int, const float*,
                                  void*, size_t, cudaStream_t);
 
 // ---- Gram: out = A' B ----------------------------------------------------------
+// grid.z splits the N rows; each block writes its 16 x 16 partial tile, and a
+// second kernel sums the splits in ascending order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) gram_kernel(int N, int p1, int p2, const T* __restrict__ A,
-                                                   const T* __restrict__ B, T* __restrict__ out) {
+__global__ void __launch_bounds__(256) gram_kernel(int N, int p1, int p2, int rows_per_split,
+                                                   const T* __restrict__ A,
+                                                   const T* __restrict__ B, T* __restrict__ part) {
   constexpr int RC = 32;
   __shared__ T As[RC][17];
   __shared__ T Bs[RC][17];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int nb = blockIdx.z * rows_per_split;
+  const int ne = min(N, nb + rows_per_split);
   T acc = T(0);
-  for (int n0 = 0; n0 < N; n0 += RC) {
+  for (int n0 = nb; n0 < ne; n0 += RC) {
     for (int t = threadIdx.x; t < RC * 16; t += 256) {
       const int rr = t / 16, cc = t % 16;
       const int n = n0 + rr;
-      As[rr][cc] = (n < N && i0 + cc < p1) ? A[size_t(n) * p1 + i0 + cc] : T(0);
-      Bs[rr][cc] = (n < N && j0 + cc < p2) ? B[size_t(n) * p2 + j0 + cc] : T(0);
+      As[rr][cc] = (n < ne && i0 + cc < p1) ? A[size_t(n) * p1 + i0 + cc] : T(0);
+      Bs[rr][cc] = (n < ne && j0 + cc < p2) ? B[size_t(n) * p2 + j0 + cc] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int rr = 0; rr < RC; ++rr) acc = fma(As[rr][ty], Bs[rr][tx], acc);
     __syncthreads();
   }
-  if (i0 + ty < p1 && j0 + tx < p2) out[size_t(i0 + ty) * p2 + j0 + tx] = acc;
+  if (i0 + ty < p1 && j0 + tx < p2)
+    part[size_t(blockIdx.z) * p1 * p2 + size_t(i0 + ty) * p2 + j0 + tx] = acc;
 }
 
 template <typename T>
-void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, cudaStream_t s) {
-  dim3 grid((p2 + 15) / 16, (p1 + 15) / 16);
-  count_launches(1);
-  gram_kernel<T><<<grid, 256, 0, s>>>(N, p1, p2, A, B, out);
+__global__ void gram_reduce_kernel(int n, int splits, const T* __restrict__ part,
+                                   T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = T(0);
+  for (int z = 0; z < splits; ++z) s += part[size_t(z) * n + i];
+  out[i] = s;
+}
+
+template <typename T>
+void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, void* ws,
+                 size_t ws_bytes, cudaStream_t s) {
+  const int gx = (p2 + 15) / 16, gy = (p1 + 15) / 16;
+  int splits = (2 * 152 + gx * gy - 1) / (gx * gy);
+  splits = std::min(splits, (N + 63) / 64);
+  const size_t per = size_t(p1) * p2 * sizeof(T);
+  if (size_t(splits) * per > ws_bytes) splits = int(ws_bytes / per);
+  if (splits < 1) splits = 1;
+  int rows = (N + splits - 1) / splits;
+  rows = (rows + 31) / 32 * 32;
+  splits = (N + rows - 1) / rows;
+  if (splits < 1) splits = 1;
+  dim3 grid(gx, gy, splits);
+  count_launches(2);
+  gram_kernel<T><<<grid, 256, 0, s>>>(N, p1, p2, rows, A, B, static_cast<T*>(ws));
+  const int n = p1 * p2;
+  gram_reduce_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, splits, static_cast<T*>(ws), out);
   MDS_CUDA(cudaGetLastError());
 }
-template void launch_gram<double>(int, int, int, const double*, const double*, double*,
-                                  cudaStream_t);
-template void launch_gram<float>(int, int, int, const float*, const float*, float*, cudaStream_t);
+template void launch_gram<double>(int, int, int, const double*, const double*, double*, void*,
+                                  size_t, cudaStream_t);
+template void launch_gram<float>(int, int, int, const float*, const float*, float*, void*, size_t,
+                                 cudaStream_t);
 
 // ---- row-local kernels: one warp per row ---------------------------------------
 template <typename T>
