@@ -79,13 +79,16 @@ typedef struct {
   double tol_grad_min, tol_grad_max, tol_grad_factor;
   double rank_tol, neg_tol, tcg_floor;
   double tcg_abs;         /* tCG also stops once ||r_j|| <= tcg_abs * eps_k */
-  int32_t p0, p_min, p_max, delta_max;
+  int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 256 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */
   int32_t precision_mode; /* MANIDSDP_PREC_* */
   int32_t verbose;        /* 1: one line per outer iteration on stderr */
   int32_t profile;        /* 1: time each phase with CUDA events on the context's
                              stream (fills the ms_* fields of the report) */
+  int32_t tcg_device;     /* 1 (default): each tCG run is one CUDA-graph launch whose
+                             WHILE node loops on the device; 0: host-driven loop */
+  int32_t reserved;
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
         "tcg_abs")] + [
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
-            "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile")]
+            "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile", "tcg_device",
+            "reserved")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -19,6 +19,8 @@ using namespace mds;
 namespace mds {
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_now() { return g_launches.load(); }
+void uncount_launches(long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 }  // namespace mds
 
 namespace {
@@ -187,6 +189,8 @@ struct manidsdp_ctx {
   double *part = nullptr, *out2 = nullptr, *dpart = nullptr;
   void* gws = nullptr;
   size_t gws_bytes = 0;
+  void* gws2 = nullptr;  // Gram partials (separate from the GEMM partials they coexist with)
+  size_t gws2_bytes = 0;
   // Lanczos
   int kmax = 0;
   double *LV = nullptr, *lh = nullptr, *lw = nullptr, *ls = nullptr;
@@ -203,6 +207,19 @@ struct manidsdp_ctx {
   double hv_psum = 0.0;
   double ms_hv = 0.0, ms_eval = 0.0, ms_grad = 0.0, ms_lz = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device-driven tCG: state, partial sums, capture stream and cached graphs
+  void* tcgst = nullptr;
+  double *kpart = nullptr, *rpart = nullptr;
+  cudaStream_t cs = nullptr;
+  struct Graph {
+    int p, prec;
+    double sigma;
+    const void *Y, *G;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long long body_launches;
+  };
+  std::vector<Graph> graphs;
 };
 
 namespace {
@@ -273,41 +290,32 @@ double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
   return std::sqrt(gg);
 }
 
-// HU = Hess Psi(Y)[P_Y(U)] using G, Gf and z of the last evaluation at Y.
+// HU = Hess Psi(Y)[P_Y(U)] using G, Gf and z of the last evaluation at Y:
+// prologue (projection, FP32 copies), class means w, split-K gather GEMM
+// G U - sigma A*(w) Y, the Gram pair [U'Y; Y'Y], then the row epilogue.
 void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* HU, int prec) {
   const int N = c->N;
-  const size_t np = size_t(N) * p;
   tstart(c);
-  launch_proj_tangent(N, p, Y, U, c->Up, c->s);
   if (prec == MANIDSDP_PREC_FP64) {
+    launch_hv_prep<double>(N, p, Y, U, c->Up, nullptr, nullptr, false, c->s);
     launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
                                c->s);
-    launch_gemm<double>(N, p, N, c->G, N, c->Up, p, c->Tm, p, 1.0, 0.0, c->idx, c->w, -c->sigma,
-                        Y, c->gws, c->gws_bytes, c->s);
-    launch_gram<double>(N, p, p, c->Up, Y, c->M1, c->gws, c->gws_bytes, c->s);
-    launch_gram<double>(N, p, p, Y, Y, c->M2, c->gws, c->gws_bytes, c->s);
-    launch_gemm<double>(N, p, p, Y, p, c->M1, p, c->YM, p, 1.0, 0.0, nullptr, nullptr, 0.0,
-                        nullptr, c->gws, c->gws_bytes, c->s);
-    launch_gemm<double>(N, p, p, c->Up, p, c->M2, p, c->YM, p, 1.0, 1.0, nullptr, nullptr, 0.0,
-                        nullptr, c->gws, c->gws_bytes, c->s);
-    launch_hess_epilogue<double>(N, p, c->Tm, c->YM, Y, c->Up, c->z, c->sigma, HU, c->s);
+    const int splits = launch_gemm_partials<double>(N, p, N, c->G, N, c->Up, p, c->idx, c->w,
+                                                    -c->sigma, Y, c->gws, c->gws_bytes, c->s);
+    launch_gram2<double>(N, p, c->Up, Y, Y, c->M1, c->gws2, c->gws2_bytes, c->s);
+    launch_hv_epilogue<double>(N, p, splits, static_cast<const double*>(c->gws), c->M1, Y, c->Up,
+                               c->z, c->sigma, HU, c->s);
   } else {
-    if (!c->yf_valid) {
-      launch_to_float(np, Y, c->Yf, c->s);
-      c->yf_valid = true;
-    }
-    launch_to_float(np, c->Up, c->Upf, c->s);
+    launch_hv_prep<float>(N, p, Y, U, c->Up, c->Upf, c->Yf, !c->yf_valid, c->s);
+    c->yf_valid = true;
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, c->s);
-    launch_gemm<float>(N, p, N, c->Gf, N, c->Upf, p, c->Tmf, p, 1.0f, 0.0f, c->idx, c->wf,
-                       float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
-    launch_gram<float>(N, p, p, c->Upf, c->Yf, c->M1f, c->gws, c->gws_bytes, c->s);
-    launch_gram<float>(N, p, p, c->Yf, c->Yf, c->M2f, c->gws, c->gws_bytes, c->s);
-    launch_gemm<float>(N, p, p, c->Yf, p, c->M1f, p, c->YMf, p, 1.0f, 0.0f, nullptr, nullptr,
-                       0.0f, nullptr, c->gws, c->gws_bytes, c->s);
-    launch_gemm<float>(N, p, p, c->Upf, p, c->M2f, p, c->YMf, p, 1.0f, 1.0f, nullptr, nullptr,
-                       0.0f, nullptr, c->gws, c->gws_bytes, c->s);
-    launch_hess_epilogue<float>(N, p, c->Tmf, c->YMf, c->Yf, c->Upf, c->z, c->sigma, HU, c->s);
+    const int splits = launch_gemm_partials<float>(N, p, N, c->Gf, N, c->Upf, p, c->idx, c->wf,
+                                                   float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
+                                                   c->s);
+    launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
+    launch_hv_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), c->M1f, Y, c->Up,
+                              c->z, c->sigma, HU, c->s);
   }
   tstop(c, &c->ms_hv);
   c->hessvecs++;
@@ -450,6 +458,7 @@ void default_params(manidsdp_params* p) {
   p->precision_mode = MANIDSDP_PREC_FP64;
   p->verbose = 0;
   p->profile = 0;
+  p->tcg_device = 1;
 }
 
 struct NonFinite {};
@@ -476,6 +485,13 @@ void release(manidsdp_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
+  for (auto& g : c->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
+  c->graphs.clear();
+  if (c->cs) cudaStreamDestroy(c->cs);
+  c->cs = nullptr;
 }
 
 // Reset the ALM state: XD = Xt + D with Xt given (device) or zero; sigma.
@@ -530,7 +546,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     prm = *params;
   else
     default_params(&prm);
-  if (prm.p_max < 1 || prm.p_max > 4096 || prm.p0 < 1 || prm.p0 > prm.p_max || prm.p_min < 1 ||
+  if (prm.p_max < 1 || prm.p_max > 256 || prm.p0 < 1 || prm.p0 > prm.p_max || prm.p_min < 1 ||
       prm.delta_max < 0 || prm.lanczos_k < 1)
     return MANIDSDP_E_ARG;
   // validate the index map and build the per-class inverse map on the host
@@ -585,6 +601,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     MDS_CUDA(cudaMallocHost(&c->hp, 64 * sizeof(double)));
     MDS_CUDA(cudaEventCreate(&c->ev0));
     MDS_CUDA(cudaEventCreate(&c->ev1));
+    MDS_CUDA(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
     c->idx = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
     c->mult = dalloc<double>(c, m);
@@ -644,7 +661,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     for (float** pp : fbufs) *pp = dalloc<float>(c, np);
     c->z = dalloc<double>(c, N);
     c->zt = dalloc<double>(c, N);
-    const size_t pp2 = size_t(c->pcap) * c->pcap;
+    const size_t pp2 = size_t(2) * c->pcap * c->pcap;  // [U'Y; Y'Y]
     c->M1 = dalloc<double>(c, pp2);
     c->M2 = dalloc<double>(c, pp2);
     c->M1f = dalloc<float>(c, pp2);
@@ -654,6 +671,11 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->dpart = dalloc<double>(c, 3 * kRedBlocks + 3);
     c->gws_bytes = (np + size_t(2) * 304 * 4096) * sizeof(double);
     c->gws = dalloc<double>(c, c->gws_bytes / sizeof(double));
+    c->gws2_bytes = size_t(1) << 21;
+    c->gws2 = dalloc<double>(c, c->gws2_bytes / sizeof(double));
+    c->tcgst = dalloc<double>(c, (tcg_state_bytes() + 7) / 8);
+    c->kpart = dalloc<double>(c, tcg_epilogue_blocks(N));
+    c->rpart = dalloc<double>(c, tcg_update_blocks());
     if (c->C != nullptr) {
       double cc;
       dots(c, NN, 1, c->C, c->C, &cc);
@@ -828,6 +850,105 @@ TcgOut tcg(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
   return {P.max_tcg, false};
 }
 
+void drop_graphs(manidsdp_ctx* c) {
+  for (auto& g : c->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
+  c->graphs.clear();
+}
+
+// Build the WHILE-node graph of one tCG run at the current (p, sigma, Y, G).
+manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
+  const void* Gkey = prec == MANIDSDP_PREC_MIXED ? static_cast<const void*>(c->Gf)
+                                                 : static_cast<const void*>(c->G);
+  for (auto& g : c->graphs)
+    if (g.p == p && g.prec == prec && g.sigma == c->sigma && g.Y == c->Y && g.G == Gkey) return g;
+  if (c->graphs.size() >= 4) drop_graphs(c);
+  const int N = c->N;
+  const size_t n = size_t(N) * p;
+  manidsdp_ctx::Graph G{};
+  G.p = p;
+  G.prec = prec;
+  G.sigma = c->sigma;
+  G.Y = c->Y;
+  G.G = Gkey;
+  MDS_CUDA(cudaGraphCreate(&G.graph, 0));
+  cudaGraphConditionalHandle h;
+  MDS_CUDA(cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MDS_CUDA(cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const long long l0 = launches_now();
+  MDS_CUDA(cudaStreamBeginCaptureToGraph(c->cs, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+  cudaStream_t s = c->cs;
+  const int neb = tcg_epilogue_blocks(N);
+  if (prec == MANIDSDP_PREC_FP64) {
+    launch_tcg_prep<double>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, nullptr, s);
+    launch_class_means<double>(c->cm, N, p, 1, c->Y, c->Up, nullptr, c->mult, c->piece_buf, c->w, s);
+    const int splits = launch_gemm_partials<double>(N, p, N, c->G, N, c->Up, p, c->idx, c->w,
+                                                    -c->sigma, c->Y, c->gws, c->gws_bytes, s);
+    launch_gram2<double>(N, p, c->Up, c->Y, c->Y, c->M1, c->gws2, c->gws2_bytes, s);
+    launch_tcg_epilogue<double>(N, p, splits, static_cast<const double*>(c->gws), c->M1, c->Y,
+                                c->Up, c->z, c->sigma, c->delta, c->Hd, c->kpart, s);
+  } else {
+    launch_tcg_prep<float>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, c->Upf, s);
+    float* pbf = reinterpret_cast<float*>(c->piece_buf);
+    launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, s);
+    const int splits = launch_gemm_partials<float>(N, p, N, c->Gf, N, c->Upf, p, c->idx, c->wf,
+                                                   float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
+                                                   s);
+    launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
+    launch_tcg_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), c->M1f, c->Y,
+                               c->Up, c->z, c->sigma, c->delta, c->Hd, c->kpart, s);
+  }
+  launch_tcg_alpha(neb, c->kpart, c->tcgst, s);
+  launch_tcg_update(n, c->tcgst, c->delta, c->Hd, c->eta, c->Heta, c->r, c->rpart, s);
+  launch_tcg_beta(tcg_update_blocks(), c->rpart, c->tcgst, h, s);
+  MDS_CUDA(cudaStreamEndCapture(c->cs, &body));
+  G.body_launches = launches_now() - l0;
+  uncount_launches(G.body_launches);  // counted per executed iteration instead
+  MDS_CUDA(cudaGraphInstantiate(&G.exec, G.graph, 0));
+  c->graphs.push_back(G);
+  return c->graphs.back();
+}
+
+// tCG as one graph launch; eta, Heta hold the step and H eta on return.
+TcgOut tcg_device(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
+  const int N = c->N;
+  const size_t n = size_t(N) * p;
+  const manidsdp_params& P = c->prm;
+  const int prec = P.precision_mode;
+  if (prec == MANIDSDP_PREC_MIXED && !c->yf_valid) {
+    launch_to_float(n, c->Y, c->Yf, c->s);
+    c->yf_valid = true;
+  }
+  MDS_CUDA(cudaMemsetAsync(c->eta, 0, n * sizeof(double), c->s));
+  MDS_CUDA(cudaMemsetAsync(c->Heta, 0, n * sizeof(double), c->s));
+  MDS_CUDA(cudaMemsetAsync(c->delta, 0, n * sizeof(double), c->s));
+  MDS_CUDA(cudaMemcpyAsync(c->r, c->grad, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  const double* gg[1] = {c->grad};
+  launch_dots(n, 1, gg, gg, c->dpart, c->s);
+  launch_tcg_init(c->tcgst, c->dpart + 3 * kRedBlocks, Delta, P.tcg_floor, P.tcg_abs * tol_grad,
+                  P.max_tcg, c->s);
+  auto& G = tcg_graph_for(c, p, prec);
+  tstart(c);
+  MDS_CUDA(cudaGraphLaunch(G.exec, c->s));
+  tstop(c, &c->ms_hv);
+  int flag = 0, iters = 0;
+  tcg_read_state(c->tcgst, &flag, &iters, c->hp + 16, c->s);
+  count_launches(G.body_launches * iters);
+  c->hessvecs += iters;
+  c->hv_psum += double(p) * iters;
+  return {iters, flag == 2 || flag == 3};
+}
+
 struct RtrOut {
   int iters;
   double gnorm;
@@ -848,7 +969,7 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
   int it = 0;
   for (; it < P.max_rtr; ++it) {
     if (gn <= tol_grad) break;
-    TcgOut t = tcg(c, p, Delta, tol_grad);
+    TcgOut t = P.tcg_device ? tcg_device(c, p, Delta, tol_grad) : tcg(c, p, Delta, tol_grad);
     double d2[2];
     dots(c, n, 2, c->grad, c->eta, d2, c->eta, c->Heta);
     const double model_dec = -(d2[0] + 0.5 * d2[1]);

@@ -75,6 +75,47 @@ void launch_gemm(int M, int ncol, int K, const T* A, int lda, const T* B, int ld
                  T alpha, T beta, const int32_t* idx, const T* w, T gscale, const T* B2,
                  void* ws, size_t ws_bytes, cudaStream_t s);
 
+// Split-K partial products only (no reduce): returns the number of splits written
+// to ws as [splits][M][ncol].
+template <typename T>
+int launch_gemm_partials(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb,
+                         const int32_t* idx, const T* w, T gscale, const T* B2, void* ws,
+                         size_t ws_bytes, cudaStream_t s);
+// out = [A1' B ; A2' B] (2 p x p), A1, A2, B: N x p.
+template <typename T>
+void launch_gram2(int N, int p, const T* A1, const T* A2, const T* B, T* out, void* ws,
+                  size_t ws_bytes, cudaStream_t s);
+// Up = P_Y(U) (FP64), UpT = T(Up), YT = T(Y) if write_y.
+template <typename T>
+void launch_hv_prep(int N, int p, const double* Y, const double* U, double* Up, T* UpT, T* YT,
+                    bool write_y, cudaStream_t s);
+// HU from the split-K partials of T = G U - sigma A*(w) Y and M = [U'Y; Y'Y].
+template <typename T>
+void launch_hv_epilogue(int N, int p, int splits, const T* part, const T* M, const double* Y,
+                        const double* Up, const double* z, double sigma, double* HU,
+                        cudaStream_t s);
+// ---- device-driven tCG (kernels_tcg.cu) ----
+size_t tcg_state_bytes();
+int tcg_epilogue_blocks(int N);
+int tcg_update_blocks();
+void launch_tcg_init(void* st, const double* rr0, double delta, double floor_rel, double abs_target,
+                     int max_iters, cudaStream_t s);
+template <typename T>
+void launch_tcg_prep(int N, int p, const void* st, const double* Y, const double* r, double* delta,
+                     double* Up, T* UpT, cudaStream_t s);
+template <typename T>
+void launch_tcg_epilogue(int N, int p, int splits, const T* part, const T* M, const double* Y,
+                         const double* Up, const double* z, double sigma, const double* delta,
+                         double* Hd, double* kpart, cudaStream_t s);
+void launch_tcg_alpha(int nparts, const double* kpart, void* st, cudaStream_t s);
+void launch_tcg_update(size_t n, const void* st, const double* delta, const double* Hd,
+                       double* eta, double* Heta, double* r, double* rpart, cudaStream_t s);
+void launch_tcg_beta(int nparts, const double* rpart, void* st, cudaGraphConditionalHandle h,
+                     cudaStream_t s);
+void tcg_read_state(const void* st, int* flag, int* iters, void* pinned, cudaStream_t s);
+long long launches_now();
+void uncount_launches(long long n);
+
 // out[p1 x p2] = A[N x p1]' B[N x p2]  (deterministic: one block per output tile,
 // a fixed reduction order over N).
 template <typename T>

@@ -103,9 +103,9 @@ __global__ void splitk_reduce_kernel(int M, int ncol, int splits, const T* __res
 }
 
 template <typename T, int BM, int BN, int TM, int TN>
-static void gemm_cfg(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb, T* out,
-                     int ldc, T alpha, T beta, const int32_t* idx, const T* w, T gscale,
-                     const T* B2, void* ws, size_t ws_bytes, cudaStream_t s) {
+static int gemm_cfg(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb, T* out,
+                    int ldc, T alpha, T beta, const int32_t* idx, const T* w, T gscale,
+                    const T* B2, void* ws, size_t ws_bytes, cudaStream_t s, bool partial_only) {
   const int gx = (ncol + BN - 1) / BN, gy = (M + BM - 1) / BM;
   int splits = (2 * 152 + gx * gy - 1) / (gx * gy);
   const int max_splits = (K + 63) / 64;
@@ -122,7 +122,7 @@ static void gemm_cfg(int M, int ncol, int K, const T* A, int lda, const T* B, in
   T* part = static_cast<T*>(ws);
   dim3 grid(gx, gy, splits);
   constexpr int NT = (BM / TM) * (BN / TN);
-  count_launches(2);
+  count_launches(partial_only ? 1 : 2);
   if (idx != nullptr)
     gemm_kernel<T, BM, BN, TM, TN, true><<<grid, NT, 0, s>>>(M, ncol, K, kchunk, A, lda, B, ldb,
                                                              idx, w, gscale, B2, part);
@@ -130,28 +130,52 @@ static void gemm_cfg(int M, int ncol, int K, const T* A, int lda, const T* B, in
     gemm_kernel<T, BM, BN, TM, TN, false><<<grid, NT, 0, s>>>(M, ncol, K, kchunk, A, lda, B, ldb,
                                                               nullptr, nullptr, T(0), nullptr,
                                                               part);
-  const size_t n = size_t(M) * ncol;
-  int rb = int((n + 255) / 256);
-  if (rb > 4096) rb = 4096;
-  splitk_reduce_kernel<T><<<rb, 256, 0, s>>>(M, ncol, splits, part, out, ldc, alpha, beta);
+  if (!partial_only) {
+    const size_t n = size_t(M) * ncol;
+    int rb = int((n + 255) / 256);
+    if (rb > 4096) rb = 4096;
+    splitk_reduce_kernel<T><<<rb, 256, 0, s>>>(M, ncol, splits, part, out, ldc, alpha, beta);
+  }
   MDS_CUDA(cudaGetLastError());
+  return splits;
+}
+
+template <typename T>
+static int gemm_any(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb, T* out,
+                    int ldc, T alpha, T beta, const int32_t* idx, const T* w, T gscale,
+                    const T* B2, void* ws, size_t ws_bytes, cudaStream_t s, bool partial_only) {
+  if (M <= 0 || ncol <= 0) return 0;
+  if (ncol <= 8)
+    return gemm_cfg<T, 128, 8, 4, 1>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w,
+                                     gscale, B2, ws, ws_bytes, s, partial_only);
+  if (ncol <= 32)
+    return gemm_cfg<T, 64, 32, 4, 2>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w,
+                                     gscale, B2, ws, ws_bytes, s, partial_only);
+  return gemm_cfg<T, 64, 64, 4, 4>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w,
+                                   gscale, B2, ws, ws_bytes, s, partial_only);
 }
 
 template <typename T>
 void launch_gemm(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb, T* out, int ldc,
                  T alpha, T beta, const int32_t* idx, const T* w, T gscale, const T* B2,
                  void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (M <= 0 || ncol <= 0) return;
-  if (ncol <= 8)
-    gemm_cfg<T, 128, 8, 4, 1>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w, gscale,
-                              B2, ws, ws_bytes, s);
-  else if (ncol <= 32)
-    gemm_cfg<T, 64, 32, 4, 2>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w, gscale,
-                              B2, ws, ws_bytes, s);
-  else
-    gemm_cfg<T, 64, 64, 4, 4>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w, gscale,
-                              B2, ws, ws_bytes, s);
+  gemm_any<T>(M, ncol, K, A, lda, B, ldb, out, ldc, alpha, beta, idx, w, gscale, B2, ws, ws_bytes,
+              s, false);
 }
+
+template <typename T>
+int launch_gemm_partials(int M, int ncol, int K, const T* A, int lda, const T* B, int ldb,
+                         const int32_t* idx, const T* w, T gscale, const T* B2, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  return gemm_any<T>(M, ncol, K, A, lda, B, ldb, nullptr, ncol, T(1), T(0), idx, w, gscale, B2, ws,
+                     ws_bytes, s, true);
+}
+template int launch_gemm_partials<double>(int, int, int, const double*, int, const double*, int,
+                                          const int32_t*, const double*, double, const double*,
+                                          void*, size_t, cudaStream_t);
+template int launch_gemm_partials<float>(int, int, int, const float*, int, const float*, int,
+                                         const int32_t*, const float*, float, const float*, void*,
+                                         size_t, cudaStream_t);
 
 template void launch_gemm<double>(int, int, int, const double*, int, const double*, int, double*,
                                   int, double, double, const int32_t*, const double*, double,
@@ -191,6 +215,39 @@ __global__ void __launch_bounds__(256) gram_kernel(int N, int p1, int p2, int ro
     part[size_t(blockIdx.z) * p1 * p2 + size_t(i0 + ty) * p2 + j0 + tx] = acc;
 }
 
+// Two Gram matrices in one launch: blockIdx.y < gy -> part1 = A1' B, else part2 = A2' B.
+template <typename T>
+__global__ void __launch_bounds__(256) gram2_kernel(int N, int p, int gy, int rows_per_split,
+                                                    const T* __restrict__ A1,
+                                                    const T* __restrict__ A2,
+                                                    const T* __restrict__ B,
+                                                    T* __restrict__ part) {
+  constexpr int RC = 32;
+  __shared__ T As[RC][17];
+  __shared__ T Bs[RC][17];
+  const int which = blockIdx.y >= gy ? 1 : 0;
+  const T* A = which ? A2 : A1;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = (blockIdx.y - which * gy) * 16, j0 = blockIdx.x * 16;
+  const int nb = blockIdx.z * rows_per_split;
+  const int ne = min(N, nb + rows_per_split);
+  T acc = T(0);
+  for (int n0 = nb; n0 < ne; n0 += RC) {
+    for (int t = threadIdx.x; t < RC * 16; t += 256) {
+      const int rr = t / 16, cc = t % 16;
+      const int n = n0 + rr;
+      As[rr][cc] = (n < ne && i0 + cc < p) ? A[size_t(n) * p + i0 + cc] : T(0);
+      Bs[rr][cc] = (n < ne && j0 + cc < p) ? B[size_t(n) * p + j0 + cc] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < RC; ++rr) acc = fma(As[rr][ty], Bs[rr][tx], acc);
+    __syncthreads();
+  }
+  if (i0 + ty < p && j0 + tx < p)
+    part[(size_t(blockIdx.z) * 2 + which) * p * p + size_t(i0 + ty) * p + j0 + tx] = acc;
+}
+
 template <typename T>
 __global__ void gram_reduce_kernel(int n, int splits, const T* __restrict__ part,
                                    T* __restrict__ out) {
@@ -223,6 +280,32 @@ void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, void* ws
 }
 template void launch_gram<double>(int, int, int, const double*, const double*, double*, void*,
                                   size_t, cudaStream_t);
+
+// out[0 : p*p] = A1' B, out[p*p : 2*p*p] = A2' B (A1, A2, B: N x p).
+template <typename T>
+void launch_gram2(int N, int p, const T* A1, const T* A2, const T* B, T* out, void* ws,
+                  size_t ws_bytes, cudaStream_t s) {
+  const int gx = (p + 15) / 16, gy = (p + 15) / 16;
+  int splits = (2 * 152 + 2 * gx * gy - 1) / (2 * gx * gy);
+  splits = std::min(splits, (N + 63) / 64);
+  const size_t per = size_t(2) * p * p * sizeof(T);
+  if (size_t(splits) * per > ws_bytes) splits = int(ws_bytes / per);
+  if (splits < 1) splits = 1;
+  int rows = (N + splits - 1) / splits;
+  rows = (rows + 31) / 32 * 32;
+  splits = (N + rows - 1) / rows;
+  if (splits < 1) splits = 1;
+  dim3 grid(gx, 2 * gy, splits);
+  count_launches(2);
+  gram2_kernel<T><<<grid, 256, 0, s>>>(N, p, gy, rows, A1, A2, B, static_cast<T*>(ws));
+  const int n = 2 * p * p;
+  gram_reduce_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, splits, static_cast<T*>(ws), out);
+  MDS_CUDA(cudaGetLastError());
+}
+template void launch_gram2<double>(int, int, const double*, const double*, const double*, double*,
+                                   void*, size_t, cudaStream_t);
+template void launch_gram2<float>(int, int, const float*, const float*, const float*, float*,
+                                  void*, size_t, cudaStream_t);
 template void launch_gram<float>(int, int, int, const float*, const float*, float*, void*, size_t,
                                  cudaStream_t);
 
@@ -263,6 +346,97 @@ template void launch_hess_epilogue<double>(int, int, const double*, const double
 template void launch_hess_epilogue<float>(int, int, const float*, const float*, const float*,
                                           const float*, const double*, double, double*,
                                           cudaStream_t);
+
+// Hessian prologue: Up = P_Y(U) in FP64; UpT = T(Up); YT = T(Y) when write_y.
+template <typename T>
+__global__ void hv_prep_kernel(int N, int p, const double* __restrict__ Y,
+                               const double* __restrict__ U, double* __restrict__ Up,
+                               T* __restrict__ UpT, T* __restrict__ YT, int write_y) {
+  const int lane = threadIdx.x % 32;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (row >= N) return;
+  const size_t o = size_t(row) * p;
+  double d = 0.0;
+  for (int c = lane; c < p; c += 32) d = fma(U[o + c], Y[o + c], d);
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+  for (int c = lane; c < p; c += 32) {
+    const double up = fma(-d, Y[o + c], U[o + c]);
+    Up[o + c] = up;
+    if (UpT != nullptr) UpT[o + c] = T(up);
+    if (write_y) YT[o + c] = T(Y[o + c]);
+  }
+}
+
+template <typename T>
+void launch_hv_prep(int N, int p, const double* Y, const double* U, double* Up, T* UpT, T* YT,
+                    bool write_y, cudaStream_t s) {
+  count_launches(1);
+  hv_prep_kernel<T><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, Y, U, Up, UpT, YT, write_y ? 1 : 0);
+  MDS_CUDA(cudaGetLastError());
+}
+template void launch_hv_prep<double>(int, int, const double*, const double*, double*, double*,
+                                     double*, bool, cudaStream_t);
+template void launch_hv_prep<float>(int, int, const double*, const double*, double*, float*,
+                                    float*, bool, cudaStream_t);
+
+// Hessian epilogue with the split-K sum of T = G U - sigma A*(w) Y and the Gram
+// products folded in:  Ht = 2 T + 2 sigma (Y M1 + Up M2),
+// HU = Ht - (Ht . Y_b) Y_b - 2 z_b Up_b   (Eq. (4.7)); M = [M1; M2] (2 p x p).
+template <typename T>
+__global__ void hv_epilogue_kernel(int N, int p, int splits, const T* __restrict__ part,
+                                   const T* __restrict__ M, const double* __restrict__ Y,
+                                   const double* __restrict__ Up, const double* __restrict__ z,
+                                   double sigma, double* __restrict__ HU) {
+  const int lane = threadIdx.x % 32;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (row >= N) return;
+  const size_t o = size_t(row) * p;
+  const size_t np = size_t(N) * p;
+  const T* M1 = M;
+  const T* M2 = M + size_t(p) * p;
+  constexpr int MAXC = 8;  // columns per lane held in registers (p <= 256)
+  double ht[MAXC];
+  double d = 0.0;
+#pragma unroll
+  for (int t = 0; t < MAXC; ++t) {
+    const int c = lane + 32 * t;
+    ht[t] = 0.0;
+    if (c < p) {
+      T tv = T(0);
+      for (int zz = 0; zz < splits; ++zz) tv += part[zz * np + o + c];
+      T ym = T(0);
+      for (int k = 0; k < p; ++k) {
+        ym = fma(T(Y[o + k]), M1[size_t(k) * p + c], ym);
+        ym = fma(T(Up[o + k]), M2[size_t(k) * p + c], ym);
+      }
+      ht[t] = 2.0 * double(tv) + 2.0 * sigma * double(ym);
+      d = fma(ht[t], Y[o + c], d);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+  const double zz2 = 2.0 * z[row];
+#pragma unroll
+  for (int t = 0; t < MAXC; ++t) {
+    const int c = lane + 32 * t;
+    if (c < p) HU[o + c] = ht[t] - d * Y[o + c] - zz2 * Up[o + c];
+  }
+}
+
+template <typename T>
+void launch_hv_epilogue(int N, int p, int splits, const T* part, const T* M, const double* Y,
+                        const double* Up, const double* z, double sigma, double* HU,
+                        cudaStream_t s) {
+  count_launches(1);
+  hv_epilogue_kernel<T><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, splits, part, M, Y, Up, z,
+                                                            sigma, HU);
+  MDS_CUDA(cudaGetLastError());
+}
+template void launch_hv_epilogue<double>(int, int, int, const double*, const double*,
+                                         const double*, const double*, const double*, double,
+                                         double*, cudaStream_t);
+template void launch_hv_epilogue<float>(int, int, int, const float*, const float*, const double*,
+                                        const double*, const double*, double, double*,
+                                        cudaStream_t);
 
 // MODE 0: out = U - (U.Y) Y ; MODE 1: out = (Y + t E) / ||Y + t E|| ; MODE 2: out[row] = A.B
 template <int MODE>

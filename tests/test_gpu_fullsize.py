@@ -1,0 +1,48 @@
+"""Parity at the benchmark's size: dense BQP order-2 relaxation, q = 80
+(N = 3241, m = 1,666,981), through the C ABI against the FP64 oracle.
+Index map and right-hand side bit-exact; Psi, grad, z, y and the Hessian-vector
+product at p = 15 (p_0 = ceil(ln m)) and p = 100 (the large-p kernel paths),
+with the same tolerances as the small cases (see test_gpu_parity)."""
+import numpy as np
+import pytest
+
+import paper_2512_04406_gb300 as mds
+from oracle import subproblem as sp
+from tests.gpu_util import instance, random_state, relerr, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    inst = instance(80, seed=0)
+    assert np.array_equal(inst["idx"], inst["prob"]["idx"])
+    assert np.array_equal(inst["b"], inst["prob"]["b"])
+    return inst
+
+
+@pytest.mark.parametrize("p", [15, 100])
+def test_q80_eval_and_hessvec(big, p):
+    torch = torch_cuda()
+    prob = big["prob"]
+    Y, Xt, U = random_state(big, p, seed=p, xt_scale=0.05)
+    sigma = 2.5
+    ctx = mds.manidsdp_setup(big["N"], big["m"], big["idx"], big["b"])
+    try:
+        mds.manidsdp_set_state(ctx, Xt, sigma)
+        Yd = torch.tensor(Y, device="cuda"); Ud = torch.tensor(U, device="cuda")
+        g = torch.empty_like(Yd)
+        z = torch.empty(big["N"], dtype=torch.float64, device="cuda")
+        psi, rn = mds.manidsdp_subproblem_eval(ctx, Yd, p, g, z)
+        G = sp.egrad_S(Y, prob, Xt, sigma)
+        assert abs(psi - sp.cost(Y, prob, Xt, sigma)) <= 1e-12 * abs(sp.cost(Y, prob, Xt, sigma))
+        assert relerr(g.cpu().numpy(), sp.proj_tangent(Y, 2 * G @ Y)) <= 1e-12
+        assert relerr(z.cpu().numpy(), sp.rowdot(G @ Y, Y)) <= 1e-12
+        H_ref = sp.rhess(Y, U, prob, Xt, sigma, G)
+        HU = torch.empty_like(Yd)
+        mds.manidsdp_hessvec(ctx, Yd, Ud, p, HU, mds.PREC_FP64)
+        assert relerr(HU.cpu().numpy(), H_ref) <= 1e-12
+        mds.manidsdp_hessvec(ctx, Yd, Ud, p, HU, mds.PREC_MIXED)
+        assert relerr(HU.cpu().numpy(), H_ref) <= 5e-5
+    finally:
+        mds.manidsdp_destroy(ctx)
