@@ -106,10 +106,13 @@ def gpu_solve(torch, inst, p0, seed, precision=mds.PREC_FP64, **kw):
         mds.manidsdp_destroy(ctx)
 
 
-@pytest.mark.parametrize("q,seed", [(4, 0), (6, 1), (10, 0), (14, 2), (20, 0)])
-def test_solve_matches_oracle_fp64(torch, q, seed):
+@pytest.mark.parametrize("q,seed,tcg_device", [(4, 0, 1), (6, 1, 1), (10, 0, 1), (10, 0, 0),
+                                               (14, 2, 1), (20, 0, 1)])
+def test_solve_matches_oracle_fp64(torch, q, seed, tcg_device):
+    """tcg_device = 1: each tCG run is one CUDA-graph launch looping on the
+    device; 0: the host-driven loop."""
     inst = instance(q, seed)
-    rep, y, Y = gpu_solve(torch, inst, 2, seed)
+    rep, y, Y = gpu_solve(torch, inst, 2, seed, tcg_device=tcg_device)
     ref = om.solve(inst["prob"], gaussian_factor(inst["N"], 2, seed))
     assert rep.status == mds.OK and rep.eta_max <= 1e-8
     assert max(ref["eta"]) <= 1e-8
