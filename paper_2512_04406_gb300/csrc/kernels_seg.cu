@@ -120,10 +120,22 @@ template void launch_class_means<float>(const ClassMap&, int, int, int, const fl
                                         float*, cudaStream_t);
 
 // ---- G pass -----------------------------------------------------------------
-// 64 x 64 tile of entries per block, 16 x 16 threads, 4 x 4 entries per thread
-// (rows ty + 16 i, columns tx + 16 j); Y rows staged through shared memory in
-// chunks of 16 columns.
+// Upper-triangle tiles only (G, R and XD are symmetric): a 64 x 64 tile of
+// entries per block, 16 x 16 threads, 4 x 4 entries per thread (rows ty + 16 i,
+// columns tx + 16 j); Y rows staged through shared memory in chunks of 16
+// columns.  Off-diagonal tiles also write their transpose through a shared-memory
+// tile so that both writes are coalesced, and count twice in the sums.
 constexpr int GP_TILE = 64, GP_KC = 16;
+
+__device__ __forceinline__ void gp_tile_coords(int t, int nt, int* by, int* bx) {
+  int r = 0;
+  while (t >= nt - r) {
+    t -= nt - r;
+    ++r;
+  }
+  *by = r;
+  *bx = r + t;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) gpass_kernel(int N, int p, const double* __restrict__ Y,
@@ -133,11 +145,16 @@ __global__ void __launch_bounds__(256) gpass_kernel(int N, int p, const double* 
                                                     double* __restrict__ XD, double* __restrict__ G,
                                                     float* __restrict__ Gf,
                                                     double* __restrict__ part) {
-  __shared__ double Yr[GP_TILE][GP_KC + 1];
-  __shared__ double Yc[GP_TILE][GP_KC + 1];
+  __shared__ double smem[GP_TILE * (GP_TILE + 1)];  // Y chunks, then the transpose tile
   __shared__ double red[2][256];
+  double (*Yr)[GP_KC + 1] = reinterpret_cast<double (*)[GP_KC + 1]>(smem);
+  double (*Yc)[GP_KC + 1] = reinterpret_cast<double (*)[GP_KC + 1]>(smem + GP_TILE * (GP_KC + 1));
+  const int nt = (N + GP_TILE - 1) / GP_TILE;
+  int tby, tbx;
+  gp_tile_coords(blockIdx.x, nt, &tby, &tbx);
+  const bool diag = tby == tbx;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int r0 = blockIdx.y * GP_TILE, c0 = blockIdx.x * GP_TILE;
+  const int r0 = tby * GP_TILE, c0 = tbx * GP_TILE;
   double s[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -165,30 +182,53 @@ __global__ void __launch_bounds__(256) gpass_kernel(int N, int p, const double* 
     }
     __syncthreads();
   }
+  // smem now free: reuse as the transpose tile T[c_local][r_local]
+  double (*Tt)[GP_TILE + 1] = reinterpret_cast<double (*)[GP_TILE + 1]>(smem);
+  const double wgt = diag ? 1.0 : 2.0;
   double sr2 = 0.0, sxs = 0.0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= N) continue;
+    const int rl = ty + 16 * i, r = r0 + rl;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
-      if (c >= N) continue;
-      const size_t e = size_t(r) * N + c;
-      const double sv = s[i][j];
-      double rv = y[idx[e]] - sv;
-      if (C != nullptr) rv -= C[e];
-      sr2 = fma(rv, rv, sr2);
-      if (MODE == 0) {
-        const double xd = XD[e];
-        const double gv = fma(-sigma, rv, xd);
-        G[e] = gv;
-        if (Gf != nullptr) Gf[e] = float(gv);
-        sxs = fma(xd, sv, sxs);
-      } else {
-        const double xd = fma(-sigma, rv, XD[e]);
-        XD[e] = xd;
-        sxs = fma(xd, sv, sxs);
+      const int cl = tx + 16 * j, c = c0 + cl;
+      double out = 0.0;
+      if (r < N && c < N) {
+        const size_t e = size_t(r) * N + c;
+        const double sv = s[i][j];
+        double rv = y[idx[e]] - sv;
+        if (C != nullptr) rv -= C[e];
+        sr2 = fma(wgt * rv, rv, sr2);
+        if (MODE == 0) {
+          const double xd = XD[e];
+          out = fma(-sigma, rv, xd);
+          G[e] = out;
+          if (Gf != nullptr) Gf[e] = float(out);
+          sxs = fma(wgt * xd, sv, sxs);
+        } else {
+          out = fma(-sigma, rv, XD[e]);
+          XD[e] = out;
+          sxs = fma(wgt * out, sv, sxs);
+        }
+      }
+      if (!diag) Tt[cl][rl] = out;
+    }
+  }
+  if (!diag) {
+    __syncthreads();
+    // write the mirrored tile: row c0 + cl, columns r0 + rl (rl fastest across threads)
+    for (int t = threadIdx.x; t < GP_TILE * GP_TILE; t += 256) {
+      const int cl = t / GP_TILE, rl = t % GP_TILE;
+      const int r = r0 + rl, c = c0 + cl;
+      if (r < N && c < N) {
+        const size_t e = size_t(c) * N + r;
+        const double v = Tt[cl][rl];
+        if (MODE == 0) {
+          G[e] = v;
+          if (Gf != nullptr) Gf[e] = float(v);
+        } else {
+          XD[e] = v;
+        }
       }
     }
   }
@@ -203,9 +243,8 @@ __global__ void __launch_bounds__(256) gpass_kernel(int N, int p, const double* 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    part[2 * bid] = red[0][0];
-    part[2 * bid + 1] = red[1][0];
+    part[2 * blockIdx.x] = red[0][0];
+    part[2 * blockIdx.x + 1] = red[1][0];
   }
 }
 
@@ -235,20 +274,20 @@ __global__ void __launch_bounds__(256) pair_sum_kernel(int nb, const double* __r
 
 size_t gpass_partials(int N) {
   const size_t nt = (size_t(N) + GP_TILE - 1) / GP_TILE;
-  return 2 * nt * nt;
+  return nt * (nt + 1);
 }
 
 void launch_gpass(int N, int p, int mode, const double* Y, const int32_t* idx, const double* y,
                   const double* C, double sigma, double* XD, double* G, float* Gf, double* part,
                   double* out2, cudaStream_t s) {
   const int nt = (N + GP_TILE - 1) / GP_TILE;
-  dim3 grid(nt, nt);
+  const int grid = nt * (nt + 1) / 2;
   count_launches(2);
   if (mode == 0)
     gpass_kernel<0><<<grid, 256, 0, s>>>(N, p, Y, idx, y, C, sigma, XD, G, Gf, part);
   else
     gpass_kernel<1><<<grid, 256, 0, s>>>(N, p, Y, idx, y, C, sigma, XD, G, Gf, part);
-  pair_sum_kernel<<<1, 256, 0, s>>>(nt * nt, part, out2);
+  pair_sum_kernel<<<1, 256, 0, s>>>(grid, part, out2);
   MDS_CUDA(cudaGetLastError());
 }
 
