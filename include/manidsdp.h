@@ -113,6 +113,13 @@ void manidsdp_default_params(manidsdp_params* params);
  * contexts).  Lets a caller count the device work inside a timed region. */
 long long manidsdp_launch_count(void);
 
+/* Device time (ms) spent in the five stages of the Hessian-vector product since the
+ * last reset, accumulated when params.profile == 2 on the host-driven path
+ * (manidsdp_hessvec, or solves with tcg_device = 0): [0] tangent projection and
+ * FP32 copies, [1] class means w, [2] gather GEMM G U - sigma A*(w) Y,
+ * [3] Gram pair [U'Y; Y'Y], [4] row epilogue.  reset != 0 zeroes the counters. */
+int manidsdp_hessvec_stage_ms(manidsdp_ctx* ctx, double* ms5, int reset);
+
 /* Human-readable text for a status code (static storage). */
 const char* manidsdp_strerror(int status);
 

@@ -21,7 +21,7 @@ __all__ = [
     "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_subproblem_eval",
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
-    "lib_path", "manidsdp_launch_count",
+    "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -79,6 +79,7 @@ _sig = {
     "manidsdp_default_params": (None, [ctypes.POINTER(Params)]),
     "manidsdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "manidsdp_launch_count": (ctypes.c_longlong, []),
+    "manidsdp_hessvec_stage_ms": (ctypes.c_int, [Context, _dp, ctypes.c_int]),
     "manidsdp_setup": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.c_int32, ctypes.c_int64, _P,
                                       _P, ctypes.c_int32, _P, ctypes.POINTER(Params), _P]),
     "manidsdp_destroy": (None, [Context]),
@@ -144,6 +145,13 @@ def manidsdp_default_params() -> Params:
 
 def manidsdp_launch_count() -> int:
     return int(_lib.manidsdp_launch_count())
+
+
+def manidsdp_hessvec_stage_ms(ctx: Context, reset: bool = True):
+    """Per-stage device time of the Hessian-vector products (params.profile == 2)."""
+    arr = (ctypes.c_double * 5)()
+    _check(_lib.manidsdp_hessvec_stage_ms(ctx, arr, 1 if reset else 0), "manidsdp_hessvec_stage_ms")
+    return dict(zip(("prep", "class_means", "gather_gemm", "gram", "epilogue"), list(arr)))
 
 
 def manidsdp_strerror(status: int) -> str:

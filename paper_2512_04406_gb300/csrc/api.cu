@@ -174,6 +174,9 @@ struct manidsdp_ctx {
   // ALM state and N x N work
   double *XD = nullptr, *G = nullptr, *Gt = nullptr;
   float *Gf = nullptr, *Gtf = nullptr;
+  // df64 halves of G (mixed mode): Gh doubles as the FP32 G of the Hess-vec
+  float *Gh = nullptr, *Gl = nullptr, *Gth = nullptr, *Gtl = nullptr;
+  float *Yh = nullptr, *Yl = nullptr;
   // per class
   double *y = nullptr, *yt = nullptr, *w = nullptr, *piece_buf = nullptr;
   float* wf = nullptr;
@@ -207,6 +210,9 @@ struct manidsdp_ctx {
   double hv_psum = 0.0;
   double ms_hv = 0.0, ms_eval = 0.0, ms_grad = 0.0, ms_lz = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-stage Hess-vec timing (params.profile == 2, host-driven path)
+  cudaEvent_t sev[8] = {};
+  double stage_ms[8] = {};
   // device-driven tCG: state, partial sums, capture stream and cached graphs
   void* tcgst = nullptr;
   double *kpart = nullptr, *rpart = nullptr;
@@ -261,13 +267,27 @@ void dots(manidsdp_ctx* c, size_t n, int k, const double* x0, const double* y0, 
   for (int i = 0; i < k; ++i) out[i] = c->hp[i];
 }
 
-// Psi, y and G (and Gf in mixed mode) at Y.
+bool mixed(const manidsdp_ctx* c) { return c->prm.precision_mode == MANIDSDP_PREC_MIXED; }
+// The FP32 copy of G read by the mixed-precision Hess-vec.
+float* g32(manidsdp_ctx* c) { return mixed(c) ? c->Gh : c->Gf; }
+
+// Psi, y and G at Y.  FP64 mode: native FP64, G (and Gf = float(G) when given).
+// Mixed mode: df64 on the FP32 pipe, G as the float pair (Gh, Gl) and, when
+// given, also in FP64.
 void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, float* Gf,
-              double* psi, double* r2) {
+              double* psi, double* r2, float* Gh = nullptr, float* Gl = nullptr) {
   tstart(c);
   c->evals++;
-  launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y, c->s);
-  launch_gpass(c->N, p, 0, Y, c->idx, y, c->C, c->sigma, c->XD, G, Gf, c->part, c->out2, c->s);
+  if (mixed(c) && Gh != nullptr) {
+    launch_split(size_t(c->N) * p, Y, c->Yh, c->Yl, c->s);
+    launch_class_means_df(c->cm, c->N, p, c->Yh, c->Yl, c->C, c->mult, c->piece_buf, y, c->s);
+    launch_gpass_df(c->N, p, 0, c->Yh, c->Yl, c->idx, y, c->C, c->sigma, c->XD, G, Gh, Gl,
+                    c->part, c->out2, c->s);
+  } else {
+    launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y,
+                               c->s);
+    launch_gpass(c->N, p, 0, Y, c->idx, y, c->C, c->sigma, c->XD, G, Gf, c->part, c->out2, c->s);
+  }
   MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   tstop(c, &c->ms_eval);
   sync(c);
@@ -276,12 +296,18 @@ void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, flo
 }
 
 // GY = G Y, z = diag(G S), grad = 2 (GY - Diag(z) Y); returns ||grad||.
-double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
+double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G,
+                const float* Gh = nullptr, const float* Gl = nullptr) {
   const int N = c->N;
   tstart(c);
   c->grads++;
-  launch_gemm<double>(N, p, N, G, N, Y, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0, nullptr,
-                      c->gws, c->gws_bytes, c->s);
+  if (Gh != nullptr) {
+    launch_split(size_t(N) * p, Y, c->Yh, c->Yl, c->s);
+    launch_gemm_df(N, p, Gh, Gl, c->Yh, c->Yl, c->GY, c->gws, c->gws_bytes, c->s);
+  } else {
+    launch_gemm<double>(N, p, N, G, N, Y, p, c->GY, p, 1.0, 0.0, nullptr, nullptr, 0.0, nullptr,
+                        c->gws, c->gws_bytes, c->s);
+  }
   launch_rowdot(N, p, c->GY, Y, c->z, c->s);
   launch_grad_from_gy(N, p, c->GY, c->z, Y, c->grad, c->s);
   tstop(c, &c->ms_grad);
@@ -295,27 +321,49 @@ double gradient(manidsdp_ctx* c, const double* Y, int p, const double* G) {
 // G U - sigma A*(w) Y, the Gram pair [U'Y; Y'Y], then the row epilogue.
 void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* HU, int prec) {
   const int N = c->N;
+  const bool stages = c->prm.profile >= 2;
+  auto mark = [&](int i) {
+    if (stages) MDS_CUDA(cudaEventRecord(c->sev[i], c->s));
+  };
   tstart(c);
+  mark(0);
   if (prec == MANIDSDP_PREC_FP64) {
     launch_hv_prep<double>(N, p, Y, U, c->Up, nullptr, nullptr, false, c->s);
+    mark(1);
     launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
                                c->s);
+    mark(2);
     const int splits = launch_gemm_partials<double>(N, p, N, c->G, N, c->Up, p, c->idx, c->w,
                                                     -c->sigma, Y, c->gws, c->gws_bytes, c->s);
+    mark(3);
     launch_gram2<double>(N, p, c->Up, Y, Y, c->M1, c->gws2, c->gws2_bytes, c->s);
+    mark(4);
     launch_hv_epilogue<double>(N, p, splits, static_cast<const double*>(c->gws), c->M1, Y, c->Up,
                                c->z, c->sigma, HU, c->s);
   } else {
     launch_hv_prep<float>(N, p, Y, U, c->Up, c->Upf, c->Yf, !c->yf_valid, c->s);
     c->yf_valid = true;
+    mark(1);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, c->s);
-    const int splits = launch_gemm_partials<float>(N, p, N, c->Gf, N, c->Upf, p, c->idx, c->wf,
+    mark(2);
+    const int splits = launch_gemm_partials<float>(N, p, N, g32(c), N, c->Upf, p, c->idx, c->wf,
                                                    float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
                                                    c->s);
+    mark(3);
     launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
+    mark(4);
     launch_hv_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), c->M1f, Y, c->Up,
                               c->z, c->sigma, HU, c->s);
+  }
+  mark(5);
+  if (stages) {
+    MDS_CUDA(cudaEventSynchronize(c->sev[5]));
+    for (int i = 0; i < 5; ++i) {
+      float ms = 0.f;
+      MDS_CUDA(cudaEventElapsedTime(&ms, c->sev[i], c->sev[i + 1]));
+      c->stage_ms[i] += ms;
+    }
   }
   tstop(c, &c->ms_hv);
   c->hessvecs++;
@@ -485,6 +533,10 @@ void release(manidsdp_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
+  for (auto& e : c->sev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   for (auto& g : c->graphs) {
     cudaGraphExecDestroy(g.exec);
     cudaGraphDestroy(g.graph);
@@ -516,6 +568,14 @@ void set_state(manidsdp_ctx* c, const double* Xt_dev, double sigma) {
 extern "C" {
 
 long long manidsdp_launch_count(void) { return mds::g_launches.load(); }
+
+int manidsdp_hessvec_stage_ms(manidsdp_ctx* c, double* ms5, int reset) {
+  if (c == nullptr || ms5 == nullptr) return MANIDSDP_E_ARG;
+  for (int i = 0; i < 5; ++i) ms5[i] = c->stage_ms[i];
+  if (reset)
+    for (double& v : c->stage_ms) v = 0.0;
+  return MANIDSDP_OK;
+}
 
 void manidsdp_default_params(manidsdp_params* params) {
   if (params) default_params(params);
@@ -601,6 +661,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     MDS_CUDA(cudaMallocHost(&c->hp, 64 * sizeof(double)));
     MDS_CUDA(cudaEventCreate(&c->ev0));
     MDS_CUDA(cudaEventCreate(&c->ev1));
+    for (auto& e : c->sev) MDS_CUDA(cudaEventCreate(&e));
     MDS_CUDA(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
     c->idx = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
@@ -645,6 +706,12 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->Gt = dalloc<double>(c, NN);
     c->Gf = dalloc<float>(c, NN);
     c->Gtf = dalloc<float>(c, NN);
+    if (prm.precision_mode == MANIDSDP_PREC_MIXED) {
+      c->Gh = dalloc<float>(c, NN);
+      c->Gl = dalloc<float>(c, NN);
+      c->Gth = dalloc<float>(c, NN);
+      c->Gtl = dalloc<float>(c, NN);
+    }
     // per class
     c->y = dalloc<double>(c, m);
     c->yt = dalloc<double>(c, m);
@@ -657,7 +724,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     double** dbufs[] = {&c->Y, &c->Yt, &c->GY, &c->grad, &c->eta, &c->Heta, &c->r, &c->delta,
                         &c->Hd, &c->Up, &c->Tm, &c->YM, &c->U, &c->tmp, &c->Vn};
     for (double** pp : dbufs) *pp = dalloc<double>(c, np);
-    float** fbufs[] = {&c->Yf, &c->Upf, &c->Tmf, &c->YMf};
+    float** fbufs[] = {&c->Yf, &c->Upf, &c->Tmf, &c->YMf, &c->Yh, &c->Yl};
     for (float** pp : fbufs) *pp = dalloc<float>(c, np);
     c->z = dalloc<double>(c, N);
     c->zt = dalloc<double>(c, N);
@@ -738,8 +805,13 @@ int manidsdp_subproblem_eval(manidsdp_ctx* c, const double* Y, int32_t p, double
     const size_t np = size_t(c->N) * p;
     MDS_CUDA(cudaMemcpyAsync(c->Y, Y, np * sizeof(double), cudaMemcpyDefault, c->s));
     double ps, r2;
-    evaluate(c, c->Y, p, c->y, c->G, c->Gf, &ps, &r2);
-    gradient(c, c->Y, p, c->G);
+    if (mixed(c)) {
+      evaluate(c, c->Y, p, c->y, c->G, nullptr, &ps, &r2, c->Gh, c->Gl);
+      gradient(c, c->Y, p, c->G, c->Gh, c->Gl);
+    } else {
+      evaluate(c, c->Y, p, c->y, c->G, c->Gf, &ps, &r2);
+      gradient(c, c->Y, p, c->G);
+    }
     c->yf_valid = false;
     c->eval_ok = true;
     c->eval_user_Y = Y;
@@ -860,7 +932,7 @@ void drop_graphs(manidsdp_ctx* c) {
 
 // Build the WHILE-node graph of one tCG run at the current (p, sigma, Y, G).
 manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
-  const void* Gkey = prec == MANIDSDP_PREC_MIXED ? static_cast<const void*>(c->Gf)
+  const void* Gkey = prec == MANIDSDP_PREC_MIXED ? static_cast<const void*>(g32(c))
                                                  : static_cast<const void*>(c->G);
   for (auto& g : c->graphs)
     if (g.p == p && g.prec == prec && g.sigma == c->sigma && g.Y == c->Y && g.G == Gkey) return g;
@@ -901,7 +973,7 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
     launch_tcg_prep<float>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, c->Upf, s);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, s);
-    const int splits = launch_gemm_partials<float>(N, p, N, c->Gf, N, c->Upf, p, c->idx, c->wf,
+    const int splits = launch_gemm_partials<float>(N, p, N, g32(c), N, c->Upf, p, c->idx, c->wf,
                                                    float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
                                                    s);
     launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
@@ -962,10 +1034,11 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
   const double Delta_bar = M_PI * std::sqrt(double(N));
   double Delta = Delta_bar / 8.0;
   double fx, r2;
-  float* gf = P.precision_mode == MANIDSDP_PREC_MIXED ? c->Gf : nullptr;
-  evaluate(c, c->Y, p, c->y, c->G, gf, &fx, &r2);
+  const bool mx = mixed(c);
+  evaluate(c, c->Y, p, c->y, mx ? nullptr : c->G, nullptr, &fx, &r2, mx ? c->Gh : nullptr,
+           mx ? c->Gl : nullptr);
   c->yf_valid = false;
-  double gn = gradient(c, c->Y, p, c->G);
+  double gn = gradient(c, c->Y, p, c->G, mx ? c->Gh : nullptr, mx ? c->Gl : nullptr);
   int it = 0;
   for (; it < P.max_rtr; ++it) {
     if (gn <= tol_grad) break;
@@ -975,7 +1048,8 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
     const double model_dec = -(d2[0] + 0.5 * d2[1]);
     launch_retract(N, p, c->Y, c->eta, 1.0, c->Yt, c->s);
     double f_new, r2n;
-    evaluate(c, c->Yt, p, c->yt, c->Gt, gf ? c->Gtf : nullptr, &f_new, &r2n);
+    evaluate(c, c->Yt, p, c->yt, mx ? nullptr : c->Gt, nullptr, &f_new, &r2n,
+             mx ? c->Gth : nullptr, mx ? c->Gtl : nullptr);
     const double reg = std::max(1.0, std::fabs(fx)) * 1e3 * 2.220446049250313e-16;
     const double rho = (model_dec + reg > 0.0) ? (fx - f_new + reg) / (model_dec + reg) : -INFINITY;
     if (!std::isfinite(f_new)) throw NonFinite{};
@@ -987,11 +1061,12 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
       std::swap(c->Y, c->Yt);
       std::swap(c->G, c->Gt);
       std::swap(c->Gf, c->Gtf);
-      gf = P.precision_mode == MANIDSDP_PREC_MIXED ? c->Gf : nullptr;
+      std::swap(c->Gh, c->Gth);
+      std::swap(c->Gl, c->Gtl);
       std::swap(c->y, c->yt);
       fx = f_new;
       c->yf_valid = false;
-      gn = gradient(c, c->Y, p, c->G);
+      gn = gradient(c, c->Y, p, c->G, mx ? c->Gh : nullptr, mx ? c->Gl : nullptr);
     }
   }
   c->rtr_iters += it;
@@ -1032,10 +1107,12 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       // step 3a: the carried direction U = [0, V]
       if (have_U) {
         double f0, r2;
-        evaluate(c, c->Y, p, c->y, c->G, nullptr, &f0, &r2);
+        const bool mx = mixed(c);
+        evaluate(c, c->Y, p, c->y, mx ? nullptr : c->G, nullptr, &f0, &r2, mx ? c->Gh : nullptr,
+                 mx ? c->Gl : nullptr);
         c->yf_valid = false;
-        gradient(c, c->Y, p, c->G);
-        hessvec(c, c->Y, c->U, p, c->Hd, MANIDSDP_PREC_FP64);
+        gradient(c, c->Y, p, c->G, mx ? c->Gh : nullptr, mx ? c->Gl : nullptr);
+        hessvec(c, c->Y, c->U, p, c->Hd, P.precision_mode);
         double curv;
         dots(c, size_t(N) * p, 1, c->U, c->Hd, &curv);
         bool moved = false;
@@ -1044,7 +1121,8 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
           for (int i = 0; i < P.carry_halvings; ++i) {
             launch_retract(N, p, c->Y, c->U, t, c->Yt, c->s);
             double ft, r2t;
-            evaluate(c, c->Yt, p, c->yt, c->Gt, nullptr, &ft, &r2t);
+            evaluate(c, c->Yt, p, c->yt, mx ? nullptr : c->Gt, nullptr, &ft, &r2t,
+                     mx ? c->Gth : nullptr, mx ? c->Gtl : nullptr);
             if (ft <= f0 - 1e-4 * 0.5 * t * t * std::fabs(curv)) {
               std::swap(c->Y, c->Yt);
               moved = true;
@@ -1067,8 +1145,14 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
                                                    std::min(P.tol_grad_max, P.tol_grad_factor * rscale));
       RtrOut ro = rtr(c, p, tol_k);
       // steps 4-8: y at the final Y is in c->y; Xt <- Xt - sigma R
-      launch_gpass(N, p, 1, c->Y, c->idx, c->y, c->C, sigma, c->XD, nullptr, nullptr, c->part,
-                   c->out2, c->s);
+      if (mixed(c)) {
+        launch_split(size_t(N) * p, c->Y, c->Yh, c->Yl, c->s);
+        launch_gpass_df(N, p, 1, c->Yh, c->Yl, c->idx, c->y, c->C, sigma, c->XD, nullptr, nullptr,
+                        nullptr, c->part, c->out2, c->s);
+      } else {
+        launch_gpass(N, p, 1, c->Y, c->idx, c->y, c->C, sigma, c->XD, nullptr, nullptr, c->part,
+                     c->out2, c->s);
+      }
       MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
       sync(c);
       const double rnorm = std::sqrt(c->hp[0]);

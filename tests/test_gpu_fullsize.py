@@ -21,13 +21,16 @@ def big():
     return inst
 
 
+@pytest.mark.parametrize("ctx_prec", [mds.PREC_FP64, mds.PREC_MIXED])
 @pytest.mark.parametrize("p", [15, 100])
-def test_q80_eval_and_hessvec(big, p):
+def test_q80_eval_and_hessvec(big, p, ctx_prec):
     torch = torch_cuda()
     prob = big["prob"]
     Y, Xt, U = random_state(big, p, seed=p, xt_scale=0.05)
     sigma = 2.5
-    ctx = mds.manidsdp_setup(big["N"], big["m"], big["idx"], big["b"])
+    prm = mds.manidsdp_default_params()
+    prm.precision_mode = ctx_prec
+    ctx = mds.manidsdp_setup(big["N"], big["m"], big["idx"], big["b"], params=prm)
     try:
         mds.manidsdp_set_state(ctx, Xt, sigma)
         Yd = torch.tensor(Y, device="cuda"); Ud = torch.tensor(U, device="cuda")

@@ -29,13 +29,18 @@ def make_ctx(inst, params=None):
     return mds.manidsdp_setup(inst["N"], inst["m"], inst["idx"], inst["b"], params=params)
 
 
+@pytest.mark.parametrize("ctx_prec", [mds.PREC_FP64, mds.PREC_MIXED])
 @pytest.mark.parametrize("q,p", CASES)
-def test_subproblem_eval_and_hessvec_fp64(torch, q, p):
+def test_subproblem_eval_and_hessvec_fp64(torch, q, p, ctx_prec):
+    """ctx_prec FP64: native FP64 evaluation; MIXED: the evaluation runs as
+    compensated float pairs (df64) on the FP32 pipe and must meet the same 1e-12."""
     inst = instance(q, seed=q)
     prob = inst["prob"]
     Y, Xt, U = random_state(inst, p, seed=q + p)
     sigma = 1.7
-    ctx = make_ctx(inst, mds.manidsdp_default_params())
+    prm = mds.manidsdp_default_params()
+    prm.precision_mode = ctx_prec
+    ctx = make_ctx(inst, prm)
     try:
         mds.manidsdp_set_state(ctx, Xt, sigma)
         N, m = inst["N"], inst["m"]
