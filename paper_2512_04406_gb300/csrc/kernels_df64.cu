@@ -147,10 +147,15 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int r0 = tby * DT, c0 = tbx * DT;
   df64acc a[4][4];
+  double ad[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[i][j] = df64acc{0.f, 0.f};
+    for (int j = 0; j < 4; ++j) {
+      a[i][j] = df64acc{0.f, 0.f};
+      ad[i][j] = 0.0;
+    }
+  int chunk = 0;
   for (int k0 = 0; k0 < p; k0 += DKC) {
     for (int t = threadIdx.x; t < DT * DKC; t += 256) {
       const int rr = t / DKC, kk = t % DKC;
@@ -181,6 +186,16 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
         for (int j = 0; j < 4; ++j) df64_fma(a[i][j], ah[i], al[i], bh[j], bl[j]);
     }
     __syncthreads();
+    if (++chunk == 4 && k0 + DKC < p) {
+      chunk = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ad[i][j] += df64_value(a[i][j]);
+          a[i][j] = df64acc{0.f, 0.f};
+        }
+    }
   }
   double(*Tt)[DT + 1] = reinterpret_cast<double(*)[DT + 1]>(smem);
   const double wgt = diag ? 1.0 : 2.0;
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
       double out = 0.0;
       if (r < N && c < N) {
         const size_t e = size_t(r) * N + c;
-        const double sv = df64_value(a[i][j]);
+        const double sv = ad[i][j] + df64_value(a[i][j]);
         double rv = y[idx[e]] - sv;
         if (C != nullptr) rv -= C[e];
         sr2 = fma(wgt * rv, rv, sr2);
@@ -313,10 +328,15 @@ __global__ void __launch_bounds__(256) gemm_df_kernel(int N, int ncol, int kchun
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kb = blockIdx.z * kchunk, ke = min(N, kb + kchunk);
   df64acc acc[TM][TN];
+  double accd[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = df64acc{0.f, 0.f};
+    for (int j = 0; j < TN; ++j) {
+      acc[i][j] = df64acc{0.f, 0.f};
+      accd[i][j] = 0.0;
+    }
+  int chunk = 0;
   for (int k0 = kb; k0 < ke; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += 256) {
       const int r = t / BK, kk = t % BK;
@@ -352,6 +372,18 @@ __global__ void __launch_bounds__(256) gemm_df_kernel(int N, int ncol, int kchun
         for (int j = 0; j < TN; ++j) df64_fma(acc[i][j], ah[i], al[i], bh[j], bl[j]);
     }
     __syncthreads();
+    // fold the float pairs into FP64 every 64 terms: bounds the growth of the
+    // float compensation term over long (K = N) sums
+    if (++chunk == 4) {
+      chunk = 0;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          accd[i][j] += df64_value(acc[i][j]);
+          acc[i][j] = df64acc{0.f, 0.f};
+        }
+    }
   }
   double* op = part + size_t(blockIdx.z) * N * ncol;
 #pragma unroll
@@ -361,7 +393,7 @@ __global__ void __launch_bounds__(256) gemm_df_kernel(int N, int ncol, int kchun
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int c = n0 + tx * TN + j;
-      if (c < ncol) op[size_t(r) * ncol + c] = df64_value(acc[i][j]);
+      if (c < ncol) op[size_t(r) * ncol + c] = accd[i][j] + df64_value(acc[i][j]);
     }
   }
 }
