@@ -177,8 +177,10 @@ struct manidsdp_ctx {
   // df64 halves of G (mixed mode): Gh doubles as the FP32 G of the Hess-vec
   float *Gh = nullptr, *Gl = nullptr, *Gth = nullptr, *Gtl = nullptr;
   float *Yh = nullptr, *Yl = nullptr;
-  // per class
+  // per class; slot[r*N + c] (r <= c): position of entry (r, c) in the inverse map
   double *y = nullptr, *yt = nullptr, *w = nullptr, *piece_buf = nullptr;
+  int32_t* slot = nullptr;
+  float* perm = nullptr;
   float* wf = nullptr;
   // N x pcap
   int pcap = 0;
@@ -345,15 +347,16 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     c->yf_valid = true;
     mark(1);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
-    launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, c->s);
+    launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
     mark(2);
-    const int splits = launch_gemm_partials<float>(N, p, N, g32(c), N, c->Upf, p, c->idx, c->wf,
-                                                   float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
-                                                   c->s);
+    const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
+                                              float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
     mark(3);
     launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
+    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
+                static_cast<float*>(c->gws) + size_t(splits) * N * p, c->s);
     mark(4);
-    launch_hv_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), c->M1f, Y, c->Up,
+    launch_hv_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), nullptr, Y, c->Up,
                               c->z, c->sigma, HU, c->s);
   }
   mark(5);
@@ -628,11 +631,15 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
   for (int64_t a = 0; a < m; ++a) ucount[a + 1] += ucount[a];
   const int32_t n_ent = ucount[m];
   std::vector<uint32_t> ent(n_ent);
+  std::vector<int32_t> slot(NN, 0);
   {
     std::vector<int32_t> pos(ucount.begin(), ucount.end() - 1);
     for (int r = 0; r < N; ++r)
-      for (int c2 = r; c2 < N; ++c2)
-        ent[pos[idx[size_t(r) * N + c2]]++] = (uint32_t(r) << 16) | uint32_t(c2);
+      for (int c2 = r; c2 < N; ++c2) {
+        const int32_t at = pos[idx[size_t(r) * N + c2]]++;
+        ent[at] = (uint32_t(r) << 16) | uint32_t(c2);
+        slot[size_t(r) * N + c2] = at;
+      }
   }
   std::vector<int32_t> pstart, pclass, mclass, mrange;
   for (int64_t a = 0; a < m; ++a) {
@@ -718,6 +725,9 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->w = dalloc<double>(c, m);
     c->wf = dalloc<float>(c, m);
     c->piece_buf = dalloc<double>(c, pclass.size());
+    c->slot = dalloc<int32_t>(c, NN);
+    MDS_CUDA(cudaMemcpyAsync(c->slot, slot.data(), NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+    c->perm = dalloc<float>(c, n_ent);
     // N x pcap
     c->pcap = prm.p_max;
     const size_t np = size_t(N) * c->pcap;
@@ -972,12 +982,13 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
   } else {
     launch_tcg_prep<float>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, c->Upf, s);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
-    launch_class_means<float>(c->cm, N, p, 1, c->Yf, c->Upf, nullptr, c->mult, pbf, c->wf, s);
-    const int splits = launch_gemm_partials<float>(N, p, N, g32(c), N, c->Upf, p, c->idx, c->wf,
-                                                   float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
-                                                   s);
+    launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
+    const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
+                                              float(-c->sigma), c->Yf, c->gws, c->gws_bytes, s);
     launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
-    launch_tcg_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), c->M1f, c->Y,
+    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
+                static_cast<float*>(c->gws) + size_t(splits) * N * p, s);
+    launch_tcg_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), nullptr, c->Y,
                                c->Up, c->z, c->sigma, c->delta, c->Hd, c->kpart, s);
   }
   launch_tcg_alpha(neb, c->kpart, c->tcgst, s);

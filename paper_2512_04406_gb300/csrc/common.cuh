@@ -106,6 +106,21 @@ void launch_gpass_df(int N, int p, int mode, const float* Yh, const float* Yl,
 void launch_gemm_df(int N, int ncol, const float* Gh, const float* Gl, const float* Yh,
                     const float* Yl, double* out, void* ws, size_t ws_bytes, cudaStream_t s);
 
+// Tiled SDDMM class sums (kernels_sddmm.cu): out[a] = A(Y U' + U Y')_a / mult[a] in FP32.
+void launch_sddmm_means(const ClassMap& cm, int N, int p, const float* Y, const float* U,
+                        const int32_t* slot, float* perm, const double* mult, float* piece_buf,
+                        float* out, cudaStream_t s);
+
+// FP32 gather GEMM partials (kernels_gemm32.cu): [splits][N][ncol] of
+// G U - sigma A*(w) Y; returns the number of splits.
+int launch_gemm32_partials(int N, int ncol, const float* G, const float* U, const int32_t* idx,
+                           const float* w, float gscale, const float* Y, void* ws, size_t ws_bytes,
+                           cudaStream_t s);
+
+// out = scale * (Y M1 + Up M2), M = [M1; M2] (2p x p), FP32 (kernels_gemm32.cu)
+void launch_ym32(int N, int p, const float* Y, const float* Up, const float* M, float scale,
+                 float* out, cudaStream_t s);
+
 // ---- device-driven tCG (kernels_tcg.cu) ----
 size_t tcg_state_bytes();
 int tcg_epilogue_blocks(int N);

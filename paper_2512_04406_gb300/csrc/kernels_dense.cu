@@ -404,12 +404,16 @@ __global__ void hv_epilogue_kernel(int N, int p, int splits, const T* __restrict
     if (c < p) {
       T tv = T(0);
       for (int zz = 0; zz < splits; ++zz) tv += part[zz * np + o + c];
-      T ym = T(0);
-      for (int k = 0; k < p; ++k) {
-        ym = fma(T(Y[o + k]), M1[size_t(k) * p + c], ym);
-        ym = fma(T(Up[o + k]), M2[size_t(k) * p + c], ym);
+      if (M == nullptr) {
+        ht[t] = 2.0 * (double(tv) + double(part[size_t(splits) * np + o + c]));
+      } else {
+        T ym = T(0);
+        for (int k = 0; k < p; ++k) {
+          ym = fma(T(Y[o + k]), M1[size_t(k) * p + c], ym);
+          ym = fma(T(Up[o + k]), M2[size_t(k) * p + c], ym);
+        }
+        ht[t] = 2.0 * double(tv) + 2.0 * sigma * double(ym);
       }
-      ht[t] = 2.0 * double(tv) + 2.0 * sigma * double(ym);
       d = fma(ht[t], Y[o + c], d);
     }
   }

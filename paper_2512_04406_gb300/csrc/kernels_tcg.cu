@@ -71,6 +71,8 @@ __global__ void tcg_prep_kernel(int N, int p, const TcgState* __restrict__ st,
 }
 
 // Hessian epilogue (as hv_epilogue_kernel) plus per-block partials of <delta, Hd>.
+// M == nullptr: the slice `splits` of part already holds sigma (Y M1 + Up M2), so
+// Ht = 2 * (sum of splits + 1 slices).
 template <typename T>
 __global__ void __launch_bounds__(256) tcg_epilogue_kernel(
     int N, int p, int splits, const T* __restrict__ part, const T* __restrict__ M,
@@ -96,12 +98,16 @@ __global__ void __launch_bounds__(256) tcg_epilogue_kernel(
       if (c < p) {
         T tv = T(0);
         for (int zz = 0; zz < splits; ++zz) tv += part[zz * np + o + c];
-        T ym = T(0);
-        for (int k = 0; k < p; ++k) {
-          ym = fma(T(Y[o + k]), M1[size_t(k) * p + c], ym);
-          ym = fma(T(Up[o + k]), M2[size_t(k) * p + c], ym);
+        if (M == nullptr) {
+          ht[t] = 2.0 * (double(tv) + double(part[size_t(splits) * np + o + c]));
+        } else {
+          T ym = T(0);
+          for (int k = 0; k < p; ++k) {
+            ym = fma(T(Y[o + k]), M1[size_t(k) * p + c], ym);
+            ym = fma(T(Up[o + k]), M2[size_t(k) * p + c], ym);
+          }
+          ht[t] = 2.0 * double(tv) + 2.0 * sigma * double(ym);
         }
-        ht[t] = 2.0 * double(tv) + 2.0 * sigma * double(ym);
         d = fma(ht[t], Y[o + c], d);
       }
     }
