@@ -154,6 +154,11 @@ int manidsdp_set_state(manidsdp_ctx* ctx, const double* Xt, double sigma);
 /* Copy out the multiplier Xt (host or device N x N FP64). */
 int manidsdp_get_multiplier(manidsdp_ctx* ctx, double* Xt);
 
+/* Copy out Xt + D = X + Diag(z) (host or device N x N FP64): the primal matrix
+ * of (PSDP) at the current multiplier and, after manidsdp_solve, the sensitivity
+ * dV/dC of the optimal value (envelope theorem on (PSDP); Algorithm 1 steps 7-8). */
+int manidsdp_get_dual_matrix(manidsdp_ctx* ctx, double* XD);
+
 /*
  * manidsdp_subproblem_eval - value and Riemannian gradient of the ALM
  * subproblem Psi_k at Y (Section 4, Eq. (Sub-k), Proposition 4.2):

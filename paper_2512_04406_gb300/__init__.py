@@ -18,7 +18,8 @@ from .build import LIB as _LIB_PATH
 __all__ = [
     "ManidsdpError", "Params", "Report", "Context",
     "manidsdp_default_params", "manidsdp_strerror", "manidsdp_setup", "manidsdp_destroy",
-    "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_subproblem_eval",
+    "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_get_dual_matrix",
+    "manidsdp_subproblem_eval",
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
     "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms",
@@ -85,6 +86,7 @@ _sig = {
     "manidsdp_destroy": (None, [Context]),
     "manidsdp_set_state": (ctypes.c_int, [Context, _P, ctypes.c_double]),
     "manidsdp_get_multiplier": (ctypes.c_int, [Context, _P]),
+    "manidsdp_get_dual_matrix": (ctypes.c_int, [Context, _P]),
     "manidsdp_subproblem_eval": (ctypes.c_int, [Context, _P, ctypes.c_int32, _dp, _P, _P, _P,
                                                 _dp]),
     "manidsdp_hessvec": (ctypes.c_int, [Context, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
@@ -179,6 +181,11 @@ def manidsdp_set_state(ctx: Context, Xt=None, sigma: float = 1.0) -> None:
 def manidsdp_get_multiplier(ctx: Context, Xt) -> None:
     _check(_lib.manidsdp_get_multiplier(ctx, _ptr(Xt, np.float64, True)),
            "manidsdp_get_multiplier")
+
+
+def manidsdp_get_dual_matrix(ctx: Context, XD) -> None:
+    _check(_lib.manidsdp_get_dual_matrix(ctx, _ptr(XD, np.float64, True)),
+           "manidsdp_get_dual_matrix")
 
 
 def manidsdp_subproblem_eval(ctx: Context, Y, p: int, rgrad=None, z=None, y=None):

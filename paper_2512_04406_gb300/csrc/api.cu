@@ -343,8 +343,12 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     launch_hv_epilogue<double>(N, p, splits, static_cast<const double*>(c->gws), c->M1, Y, c->Up,
                                c->z, c->sigma, HU, c->s);
   } else {
-    launch_hv_prep<float>(N, p, Y, U, c->Up, c->Upf, c->Yf, !c->yf_valid, c->s);
+    const bool fresh = !c->yf_valid;
+    launch_hv_prep<float>(N, p, Y, U, c->Up, c->Upf, c->Yf, fresh, c->s);
     c->yf_valid = true;
+    if (fresh)  // Y'Y depends on Y only: second p x p slot of M1f
+      launch_gram2<float>(N, p, c->Yf, nullptr, c->Yf, c->M1f + size_t(p) * p, c->gws2,
+                          c->gws2_bytes, c->s);
     mark(1);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
@@ -352,7 +356,7 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
                                               float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
     mark(3);
-    launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
+    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
     launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
                 static_cast<float*>(c->gws) + size_t(splits) * N * p, c->s);
     mark(4);
@@ -808,6 +812,16 @@ int manidsdp_get_multiplier(manidsdp_ctx* c, double* Xt) {
   });
 }
 
+int manidsdp_get_dual_matrix(manidsdp_ctx* c, double* XD) {
+  if (c == nullptr || XD == nullptr) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    const size_t NN = size_t(c->N) * c->N;
+    MDS_CUDA(cudaMemcpyAsync(XD, c->XD, NN * sizeof(double), cudaMemcpyDefault, c->s));
+    sync(c);
+    return MANIDSDP_OK;
+  });
+}
+
 int manidsdp_subproblem_eval(manidsdp_ctx* c, const double* Y, int32_t p, double* psi,
                              double* rgrad, double* z, double* y, double* rnorm) {
   if (c == nullptr || Y == nullptr || p < 1 || p > c->pcap) return MANIDSDP_E_ARG;
@@ -985,7 +999,7 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
     launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
     const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
                                               float(-c->sigma), c->Yf, c->gws, c->gws_bytes, s);
-    launch_gram2<float>(N, p, c->Upf, c->Yf, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
+    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
     launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
                 static_cast<float*>(c->gws) + size_t(splits) * N * p, s);
     launch_tcg_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), nullptr, c->Y,
@@ -1010,6 +1024,8 @@ TcgOut tcg_device(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
   const int prec = P.precision_mode;
   if (prec == MANIDSDP_PREC_MIXED && !c->yf_valid) {
     launch_to_float(n, c->Y, c->Yf, c->s);
+    launch_gram2<float>(N, p, c->Yf, nullptr, c->Yf, c->M1f + size_t(p) * p, c->gws2,
+                        c->gws2_bytes, c->s);
     c->yf_valid = true;
   }
   MDS_CUDA(cudaMemsetAsync(c->eta, 0, n * sizeof(double), c->s));

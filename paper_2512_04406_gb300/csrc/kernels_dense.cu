@@ -215,37 +215,63 @@ __global__ void __launch_bounds__(256) gram_kernel(int N, int p1, int p2, int ro
     part[size_t(blockIdx.z) * p1 * p2 + size_t(i0 + ty) * p2 + j0 + tx] = acc;
 }
 
-// Two Gram matrices in one launch: blockIdx.y < gy -> part1 = A1' B, else part2 = A2' B.
+// Gram matrices A' B over N rows (A, B: N x p): 64 x 64 output tile per block,
+// 4 x 4 outputs per thread, rows staged 32 at a time; grid.z splits the rows and
+// each split writes its partial tile (summed in ascending order afterwards).
+// With two=true, blockIdx.y >= gy computes A2' B into the second p x p slot.
 template <typename T>
 __global__ void __launch_bounds__(256) gram2_kernel(int N, int p, int gy, int rows_per_split,
                                                     const T* __restrict__ A1,
                                                     const T* __restrict__ A2,
-                                                    const T* __restrict__ B,
+                                                    const T* __restrict__ B, int nmat,
                                                     T* __restrict__ part) {
   constexpr int RC = 32;
-  __shared__ T As[RC][17];
-  __shared__ T Bs[RC][17];
+  __shared__ T As[RC][65];
+  __shared__ T Bs[RC][65];
   const int which = blockIdx.y >= gy ? 1 : 0;
   const T* A = which ? A2 : A1;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int i0 = (blockIdx.y - which * gy) * 16, j0 = blockIdx.x * 16;
+  const int i0 = (blockIdx.y - which * gy) * 64, j0 = blockIdx.x * 64;
   const int nb = blockIdx.z * rows_per_split;
   const int ne = min(N, nb + rows_per_split);
-  T acc = T(0);
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   for (int n0 = nb; n0 < ne; n0 += RC) {
-    for (int t = threadIdx.x; t < RC * 16; t += 256) {
-      const int rr = t / 16, cc = t % 16;
+    for (int t = threadIdx.x; t < RC * 64; t += 256) {
+      const int rr = t / 64, cc = t % 64;
       const int n = n0 + rr;
       As[rr][cc] = (n < ne && i0 + cc < p) ? A[size_t(n) * p + i0 + cc] : T(0);
       Bs[rr][cc] = (n < ne && j0 + cc < p) ? B[size_t(n) * p + j0 + cc] : T(0);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < RC; ++rr) acc = fma(As[rr][ty], Bs[rr][tx], acc);
+#pragma unroll 4
+    for (int rr = 0; rr < RC; ++rr) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[rr][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[rr][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
     __syncthreads();
   }
-  if (i0 + ty < p && j0 + tx < p)
-    part[(size_t(blockIdx.z) * 2 + which) * p * p + size_t(i0 + ty) * p + j0 + tx] = acc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = i0 + ty + 16 * i;
+    if (r >= p) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = j0 + tx + 16 * j;
+      if (cc < p)
+        part[(size_t(blockIdx.z) * nmat + which) * p * p + size_t(r) * p + cc] = acc[i][j];
+    }
+  }
 }
 
 template <typename T>
@@ -281,24 +307,25 @@ void launch_gram(int N, int p1, int p2, const T* A, const T* B, T* out, void* ws
 template void launch_gram<double>(int, int, int, const double*, const double*, double*, void*,
                                   size_t, cudaStream_t);
 
-// out[0 : p*p] = A1' B, out[p*p : 2*p*p] = A2' B (A1, A2, B: N x p).
+// out[0 : p*p] = A1' B and, when A2 != nullptr, out[p*p : 2*p*p] = A2' B.
 template <typename T>
 void launch_gram2(int N, int p, const T* A1, const T* A2, const T* B, T* out, void* ws,
                   size_t ws_bytes, cudaStream_t s) {
-  const int gx = (p + 15) / 16, gy = (p + 15) / 16;
-  int splits = (2 * 152 + 2 * gx * gy - 1) / (2 * gx * gy);
+  const int nmat = A2 != nullptr ? 2 : 1;
+  const int gx = (p + 63) / 64, gy = (p + 63) / 64;
+  int splits = (2 * 152 + nmat * gx * gy - 1) / (nmat * gx * gy);
   splits = std::min(splits, (N + 63) / 64);
-  const size_t per = size_t(2) * p * p * sizeof(T);
+  const size_t per = size_t(nmat) * p * p * sizeof(T);
   if (size_t(splits) * per > ws_bytes) splits = int(ws_bytes / per);
   if (splits < 1) splits = 1;
   int rows = (N + splits - 1) / splits;
   rows = (rows + 31) / 32 * 32;
   splits = (N + rows - 1) / rows;
   if (splits < 1) splits = 1;
-  dim3 grid(gx, 2 * gy, splits);
+  dim3 grid(gx, nmat * gy, splits);
   count_launches(2);
-  gram2_kernel<T><<<grid, 256, 0, s>>>(N, p, gy, rows, A1, A2, B, static_cast<T*>(ws));
-  const int n = 2 * p * p;
+  gram2_kernel<T><<<grid, 256, 0, s>>>(N, p, gy, rows, A1, A2, B, nmat, static_cast<T*>(ws));
+  const int n = nmat * p * p;
   gram_reduce_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, splits, static_cast<T*>(ws), out);
   MDS_CUDA(cudaGetLastError());
 }
