@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--hv-reps", type=int, default=30)
+    ap.add_argument("--hv-only", type=int, default=0,
+                    help="only time the Hessian-vector product at this p (profiling)")
     return ap.parse_args()
 
 
@@ -137,13 +139,14 @@ def workload(q, seed):
 
 
 def hessvec_bytes(N, m, n_entries, n_pieces, p, fp_bytes):
-    """Algorithmic DRAM bytes of one Hessian-vector product (Proposition 4.2):
-    class-mean pass reads the inverse map (4 B per upper-triangle entry) and the
-    piece table (8 B per piece) and writes w (fp_bytes per class); the gather-GEMM
-    pass reads G (fp_bytes per entry) and the index map (4 B per entry); the
-    N x p operands Y, U are read and HU written once (8 B each in FP64 I/O)."""
-    return (4 * n_entries + 8 * n_pieces + fp_bytes * m + (fp_bytes + 4) * N * N
-            + 3 * 8 * N * p)
+    """Algorithmic DRAM bytes of one Hessian-vector product (Proposition 4.2) in
+    the tiled form: the class-sum pass reads the slot map (4 B per upper-triangle
+    entry), writes and re-reads the class-ordered buffer (2 x fp_bytes per upper
+    entry), reads the piece table (8 B per piece) and writes w (fp_bytes per
+    class); the gather GEMM reads G (fp_bytes per entry) and the index map (4 B
+    per entry); Y, U are read and HU written once (8 B each, FP64 I/O)."""
+    return ((4 + 2 * fp_bytes) * n_entries + 8 * n_pieces + fp_bytes * m
+            + (fp_bytes + 4) * N * N + 3 * 8 * N * p)
 
 
 def measure_hessvec(mds, torch, ctx, N, p, reps, precision, seed=11):
@@ -265,6 +268,16 @@ def main():
     prm.profile = 1
     stream = torch.cuda.current_stream()
     ctx = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
+    if args.hv_only:
+        p = args.hv_only
+        ms = measure_hessvec(mds, torch, ctx, N, p, args.hv_reps, prec)
+        fp_bytes = 4 if prec == mds.PREC_MIXED else 8
+        byt = hessvec_bytes(N, m, N * (N + 1) // 2, m, p, fp_bytes)
+        print(json.dumps({"hv_only": True, "q": args.q, "N": N, "p": p, "precision": args.precision,
+                          "ms": ms, "gbs": byt / (ms * 1e-3) / 1e9,
+                          "tflops": 6.0 * N * N * p / (ms * 1e-3) / 1e12}), flush=True)
+        mds.manidsdp_destroy(ctx)
+        return
     Y0 = torch.tensor(gaussian_factor(N, p0, args.seed + rank), device="cuda")
     for _ in range(args.warmup):
         mds.manidsdp_solve(ctx, Y0, p0)

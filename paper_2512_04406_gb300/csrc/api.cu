@@ -1051,6 +1051,8 @@ TcgOut tcg_device(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
 struct RtrOut {
   int iters;
   double gnorm;
+  int rejected = 0, boundary = 0;
+  double delta_end = 0.0;
 };
 
 // Riemannian trust region on Psi_k from c->Y; leaves y, G, z, grad at the final Y.
@@ -1066,7 +1068,7 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
            mx ? c->Gl : nullptr);
   c->yf_valid = false;
   double gn = gradient(c, c->Y, p, c->G, mx ? c->Gh : nullptr, mx ? c->Gl : nullptr);
-  int it = 0;
+  int it = 0, nrej = 0, nbound = 0;
   for (; it < P.max_rtr; ++it) {
     if (gn <= tol_grad) break;
     TcgOut t = P.tcg_device ? tcg_device(c, p, Delta, tol_grad) : tcg(c, p, Delta, tol_grad);
@@ -1084,6 +1086,8 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
       Delta /= 4.0;
     else if (rho > 0.75 && t.boundary)
       Delta = std::min(2.0 * Delta, Delta_bar);
+    if (t.boundary) ++nbound;
+    if (!(rho > 0.1)) ++nrej;
     if (rho > 0.1) {
       std::swap(c->Y, c->Yt);
       std::swap(c->G, c->Gt);
@@ -1098,7 +1102,11 @@ RtrOut rtr(manidsdp_ctx* c, int p, double tol_grad) {
   }
   c->rtr_iters += it;
   c->psi = fx;
-  return {it, gn};
+  RtrOut out{it, gn};
+  out.rejected = nrej;
+  out.boundary = nbound;
+  out.delta_end = Delta;
+  return out;
 }
 
 // Row-major N x p_old -> N x p_new in place through c->tmp (zero-padded columns).
@@ -1205,10 +1213,10 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       const double eta = std::max(rep.eta_p, std::max(rep.eta_d, rep.eta_g));
       if (P.verbose)
         std::fprintf(stderr,
-                     "[manidsdp] k=%d p=%d sigma=%.3g rtr=%d gnorm=%.3e eta=(%.2e %.2e %.2e) "
-                     "lmin=%.3e V=%.12f hv=%d lz=%d\n",
-                     k, p, sigma, ro.iters, ro.gnorm, rep.eta_p, rep.eta_d, rep.eta_g, lo.lo[0], by,
-                     c->hessvecs, lo.steps);
+                     "[manidsdp] k=%d p=%d sigma=%.3g rtr=%d(rej %d, bnd %d, D %.2e) gnorm=%.3e "
+                     "tol=%.2e eta=(%.2e %.2e %.2e) lmin=%.3e V=%.12f hv=%d lz=%d\n",
+                     k, p, sigma, ro.iters, ro.rejected, ro.boundary, ro.delta_end, ro.gnorm, tol_k,
+                     rep.eta_p, rep.eta_d, rep.eta_g, lo.lo[0], by, c->hessvecs, lo.steps);
       if (!std::isfinite(eta)) {
         status = MANIDSDP_E_NONFINITE;
         break;

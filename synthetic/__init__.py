@@ -4,11 +4,11 @@ This module draws random numbers only; it holds none of the solver's arithmetic
 (no index maps, no right-hand sides, no normalisation).  Both the CPU oracle and
 the CUDA path receive exactly the arrays produced here.
 
-Instance recipes follow the paper's experiments (Section 6): the dense BQP of
-Section 6.1 draws the independent entries of a symmetric Q and the entries of c
-from N(0,1); the sparse-Q variant keeps each upper-triangular entry with
-probability `density`; the UCQP draws a Hermitian Q whose real and imaginary
-parts are iid N(0,1).  Draw order is fixed so that any consumer reproduces the
+Instance recipes follow the random instances of the paper's experiments
+(Section 6): for the dense BQP of Section 6.1, Q is symmetric with standard
+normal free entries and c is standard normal; the sparse-Q variant keeps each
+upper-triangular entry with probability `density`; the Hermitian UCQP matrix
+has standard normal real and imaginary parts.  Draw order is fixed so that any consumer reproduces the
 same arrays from the same seed.
 """
 from __future__ import annotations
