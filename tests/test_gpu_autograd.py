@@ -98,20 +98,28 @@ def test_value_sensitivity_dV_dQ_finite_differences():
 
 
 def test_value_sensitivity_dV_dC_matches_dual_matrix():
-    """A dense C moves the optimum off the exact vertex, so the solves reach
-    1e-10 rather than the residue-dive level; h = 1e-4 keeps the central
-    difference's truncation and solve errors below the 1e-4 check."""
+    """dV/dC = Xt* + D: compared with the oracle's converged Xt + D, and with
+    central differences of re-solved values.  A dense C moves the optimum off the
+    exact vertex (no residue dive; the solves stall near 1e-9), so h = 1e-3 and a
+    2e-3 relative check keep truncation and solve errors below the bound."""
     torch_cuda()
+    from paper_2512_04406_gb300.autograd import value_and_sensitivities
+    from oracle import moment
     q, seed = 6, 2
     Q, c = bqp_instance(q, seed)
     N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
     b = mds.manidsdp_bqp_rhs(q, Q, c, 2)
-    prm = mds.manidsdp_default_params(); prm.tol = 1e-10; prm.max_outer = 80
-    from paper_2512_04406_gb300.autograd import value_and_sensitivities
+    prm = mds.manidsdp_default_params(); prm.tol = 1e-10; prm.max_outer = 60
     rep, y, XD = value_and_sensitivities(N, m, idx, b, gaussian_factor(N, 2, seed), prm)
+    ref_idx = moment.index_map(q)
+    prob = om.make_problem(ref_idx, moment.multiplicities(ref_idx, m), moment.rhs(q, Q, c))
+    ref = om.solve(prob, gaussian_factor(N, 2, seed), params=dict(tol=1e-10))
+    assert np.abs(XD - (ref["Xt"] + prob["D"])).max() <= 1e-6 * (1 + np.abs(XD).max())
+    assert np.abs(y - ref["y"]).max() <= 1e-6
     rng = np.random.default_rng(3)
-    h = 1e-4
-    for _ in range(4):
+    h = 1e-3
+    prm.tol = 1e-9
+    for _ in range(3):
         a, g_ = rng.choice(N, 2, replace=False)
         E = np.zeros((N, N)); E[a, g_] = E[g_, a] = 1.0
         vals = []
@@ -120,9 +128,9 @@ def test_value_sensitivity_dV_dC_matches_dual_matrix():
                                      params=prm)
             try:
                 r, _ = mds.manidsdp_solve(ctx, gaussian_factor(N, 2, seed), 2)
-                assert r.status == mds.OK
+                assert r.eta_max <= 1e-8, r.as_dict()
                 vals.append(r.value)
             finally:
                 mds.manidsdp_destroy(ctx)
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(fd - 2 * XD[a, g_]) <= 1e-4 * max(1.0, abs(fd)), (fd, 2 * XD[a, g_])
+        assert abs(fd - 2 * XD[a, g_]) <= 2e-3 * max(1.0, abs(fd)), (fd, 2 * XD[a, g_])
