@@ -72,13 +72,14 @@ typedef struct manidsdp_ctx manidsdp_ctx; /* opaque, owned by the library */
  * rank growth by at most delta_max eigenvectors whose eigenvalue is below
  * -neg_tol * (1 + |lambda_max(X)|); tCG relative-residual floor tcg_floor and
  * absolute stop tcg_abs * eps_k;
- * carried-direction line search with carry_halvings halvings from sqrt(N). */
+ * carried-direction line search with carry_halvings halvings from carry_t0. */
 typedef struct {
   double sigma0, sigma_min, sigma_max, gamma, kappa1, kappa2;
   double tol;             /* stop when eta_max <= tol (Section 6) */
   double tol_grad_min, tol_grad_max, tol_grad_factor;
   double rank_tol, neg_tol, tcg_floor;
   double tcg_abs;         /* tCG also stops once ||r_j|| <= tcg_abs * eps_k */
+  double carry_t0;        /* first step of the carried-direction line search; <= 0: sqrt(N) */
   int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 256 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */

@@ -27,7 +27,8 @@ Readings where the paper is silent (each also listed in the design notes):
     asks for ||grad|| <= eps_k, so resolving the model gradient further is wasted.
   * Use of the carried U (step 3, "supplied with"): if the exact curvature
     <U, Hess Psi_{k+1}(Yhat)[U]> (Proposition 5.1) is negative, take
-    Y <- Retr(Yhat + t U) for the largest t in sqrt(N) 2^-j, j = 0..carry_halvings-1,
+    Y <- Retr(Yhat + t U) for the largest t in t0 2^-j, j = 0..carry_halvings-1
+    (t0 = carry_t0, or sqrt(N) when carry_t0 <= 0),
     that decreases Psi_{k+1} by at least 1e-4 t^2 |<U, Hess U>| / 2;
     otherwise drop the appended columns.
   * Eigenvectors are normalised to a positive first nonzero entry.
@@ -48,7 +49,7 @@ DEFAULTS = dict(
     p0=2, p_min=2, p_max=256, delta_max=8,
     max_outer=300, max_rtr=200, max_tcg=500, tol=1e-8,
     tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1e-1, tcg_floor=1e-10, tcg_abs=0.1,
-    rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30,
+    rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0,
     lanczos_k=300,
 )
 
@@ -122,7 +123,7 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
             moved = False
             if curv < 0.0:
                 f0 = f(Y)
-                t = math.sqrt(N)
+                t = prm["carry_t0"] if prm["carry_t0"] > 0 else math.sqrt(N)
                 for _ in range(prm["carry_halvings"]):
                     Yt = sp.retract(Y, t * U)
                     if f(Yt) <= f0 - 1e-4 * 0.5 * t * t * abs(curv):

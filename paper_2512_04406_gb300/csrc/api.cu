@@ -501,6 +501,7 @@ void default_params(manidsdp_params* p) {
   p->neg_tol = 1e-10;
   p->tcg_floor = 1e-10;
   p->tcg_abs = 0.1;
+  p->carry_t0 = 0.0;
   p->p0 = 2;
   p->p_min = 2;
   p->p_max = 256;
@@ -1152,7 +1153,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
         dots(c, size_t(N) * p, 1, c->U, c->Hd, &curv);
         bool moved = false;
         if (curv < 0.0) {
-          double t = std::sqrt(double(N));
+          double t = P.carry_t0 > 0.0 ? P.carry_t0 : std::sqrt(double(N));
           for (int i = 0; i < P.carry_halvings; ++i) {
             launch_retract(N, p, c->Y, c->U, t, c->Yt, c->s);
             double ft, r2t;
