@@ -181,6 +181,8 @@ struct manidsdp_ctx {
   double *y = nullptr, *yt = nullptr, *w = nullptr, *piece_buf = nullptr;
   int32_t* slot = nullptr;
   float* perm = nullptr;
+  double* permd = nullptr;  // class-ordered FP64 values (df64 evaluation)
+  double* Sup = nullptr;    // S = Y Y' by upper tiles (df64 evaluation)
   float* wf = nullptr;
   // N x pcap
   int pcap = 0;
@@ -282,9 +284,10 @@ void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, flo
   c->evals++;
   if (mixed(c) && Gh != nullptr) {
     launch_split(size_t(c->N) * p, Y, c->Yh, c->Yl, c->s);
-    launch_class_means_df(c->cm, c->N, p, c->Yh, c->Yl, c->C, c->mult, c->piece_buf, y, c->s);
+    launch_spass_df(c->cm, c->N, p, c->Yh, c->Yl, c->C, c->slot, c->Sup, c->permd, c->mult,
+                    c->piece_buf, y, c->s);
     launch_gpass_df(c->N, p, 0, c->Yh, c->Yl, c->idx, y, c->C, c->sigma, c->XD, G, Gh, Gl,
-                    c->part, c->out2, c->s);
+                    c->part, c->out2, c->s, c->Sup);
   } else {
     launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y,
                                c->s);
@@ -733,6 +736,10 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->slot = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->slot, slot.data(), NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
     c->perm = dalloc<float>(c, n_ent);
+    if (prm.precision_mode == MANIDSDP_PREC_MIXED) {
+      c->permd = dalloc<double>(c, n_ent);
+      c->Sup = dalloc<double>(c, NN);
+    }
     // N x pcap
     c->pcap = prm.p_max;
     const size_t np = size_t(N) * c->pcap;

@@ -102,7 +102,12 @@ void launch_class_means_df(const ClassMap& cm, int N, int p, const float* Yh, co
 void launch_gpass_df(int N, int p, int mode, const float* Yh, const float* Yl,
                      const int32_t* idx, const double* y, const double* C, double sigma,
                      double* XD, double* G, float* Gh, float* Gl, double* part, double* out2,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* Sup = nullptr);
+// y(S) by tiles: S = Y Y' (df64) into Sup (N x N, tiles of the upper triangle), class
+// sums through the slot map into permd, per-piece FP64 sums into y.
+void launch_spass_df(const ClassMap& cm, int N, int p, const float* Yh, const float* Yl,
+                     const double* C, const int32_t* slot, double* Sup, double* permd,
+                     const double* mult, double* piece_buf, double* y, cudaStream_t s);
 void launch_gemm_df(int N, int ncol, const float* Gh, const float* Gl, const float* Yh,
                     const float* Yl, double* out, void* ws, size_t ws_bytes, cudaStream_t s);
 

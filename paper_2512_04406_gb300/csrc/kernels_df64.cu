@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
     int N, int p, const float* __restrict__ Yh, const float* __restrict__ Yl,
     const int32_t* __restrict__ idx, const double* __restrict__ y, const double* __restrict__ C,
     double sigma, double* __restrict__ XD, double* __restrict__ G, float* __restrict__ Gh,
-    float* __restrict__ Gl, double* __restrict__ part) {
+    float* __restrict__ Gl, double* __restrict__ part, const double* __restrict__ Sup) {
   __shared__ double smem[DT * (DT + 1)];  // float Y chunks, then the transpose tile
   __shared__ double red[2][256];
   float(*Rh)[DKC + 1] = reinterpret_cast<float(*)[DKC + 1]>(smem);
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
       ad[i][j] = 0.0;
     }
   int chunk = 0;
-  for (int k0 = 0; k0 < p; k0 += DKC) {
+  for (int k0 = 0; k0 < (Sup == nullptr ? p : 0); k0 += DKC) {
     for (int t = threadIdx.x; t < DT * DKC; t += 256) {
       const int rr = t / DKC, kk = t % DKC;
       const int gr = r0 + rr, gc = c0 + rr, k = k0 + kk;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) gpass_df_kernel(
       double out = 0.0;
       if (r < N && c < N) {
         const size_t e = size_t(r) * N + c;
-        const double sv = ad[i][j] + df64_value(a[i][j]);
+        const double sv = Sup != nullptr ? Sup[e] : ad[i][j] + df64_value(a[i][j]);
         double rv = y[idx[e]] - sv;
         if (C != nullptr) rv -= C[e];
         sr2 = fma(wgt * rv, rv, sr2);
@@ -298,15 +298,137 @@ __global__ void __launch_bounds__(256) df_pair_sum_kernel(int nb, const double* 
 void launch_gpass_df(int N, int p, int mode, const float* Yh, const float* Yl,
                      const int32_t* idx, const double* y, const double* C, double sigma,
                      double* XD, double* G, float* Gh, float* Gl, double* part, double* out2,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* Sup) {
   const int nt = (N + DT - 1) / DT;
   const int grid = nt * (nt + 1) / 2;
   count_launches(2);
   if (mode == 0)
-    gpass_df_kernel<0><<<grid, 256, 0, s>>>(N, p, Yh, Yl, idx, y, C, sigma, XD, G, Gh, Gl, part);
+    gpass_df_kernel<0><<<grid, 256, 0, s>>>(N, p, Yh, Yl, idx, y, C, sigma, XD, G, Gh, Gl, part,
+                                            Sup);
   else
-    gpass_df_kernel<1><<<grid, 256, 0, s>>>(N, p, Yh, Yl, idx, y, C, sigma, XD, G, Gh, Gl, part);
+    gpass_df_kernel<1><<<grid, 256, 0, s>>>(N, p, Yh, Yl, idx, y, C, sigma, XD, G, Gh, Gl, part,
+                                            Sup);
   df_pair_sum_kernel<<<1, 256, 0, s>>>(grid, part, out2);
+  MDS_CUDA(cudaGetLastError());
+}
+
+// ---- tiled y(S): S = Y Y' once, df64, upper-triangle tiles --------------------------------
+// Writes S[r, c] for every entry of the tile to Sup (the G pass then reads it instead
+// of recomputing the dot products) and wt * (S + C) of each upper entry (r <= c) to
+// its slot of the class-ordered buffer permd (wt = 2 off the diagonal).
+__global__ void __launch_bounds__(256) spass_df_kernel(int N, int p, const float* __restrict__ Yh,
+                                                       const float* __restrict__ Yl,
+                                                       const double* __restrict__ C,
+                                                       const int32_t* __restrict__ slot,
+                                                       double* __restrict__ Sup,
+                                                       double* __restrict__ permd) {
+  __shared__ float Rh[DT][DKC + 1], Rl[DT][DKC + 1], Ch[DT][DKC + 1], Cl[DT][DKC + 1];
+  const int nt = (N + DT - 1) / DT;
+  int tby, tbx;
+  df_tile_coords(blockIdx.x, nt, &tby, &tbx);
+  const bool diag = tby == tbx;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r0 = tby * DT, c0 = tbx * DT;
+  df64acc a[4][4];
+  double ad[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a[i][j] = df64acc{0.f, 0.f};
+      ad[i][j] = 0.0;
+    }
+  int chunk = 0;
+  for (int k0 = 0; k0 < p; k0 += DKC) {
+    for (int t = threadIdx.x; t < DT * DKC; t += 256) {
+      const int rr = t / DKC, kk = t % DKC;
+      const int gr = r0 + rr, gc = c0 + rr, k = k0 + kk;
+      const bool okr = gr < N && k < p, okc = gc < N && k < p;
+      Rh[rr][kk] = okr ? Yh[size_t(gr) * p + k] : 0.f;
+      Rl[rr][kk] = okr ? Yl[size_t(gr) * p + k] : 0.f;
+      Ch[rr][kk] = okc ? Yh[size_t(gc) * p + k] : 0.f;
+      Cl[rr][kk] = okc ? Yl[size_t(gc) * p + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < DKC; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Rh[ty + 16 * i][kk];
+        al[i] = Rl[ty + 16 * i][kk];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bh[j] = Ch[tx + 16 * j][kk];
+        bl[j] = Cl[tx + 16 * j][kk];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df64_fma(a[i][j], ah[i], al[i], bh[j], bl[j]);
+    }
+    __syncthreads();
+    if (++chunk == 4 && k0 + DKC < p) {
+      chunk = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ad[i][j] += df64_value(a[i][j]);
+          a[i][j] = df64acc{0.f, 0.f};
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rl = ty + 16 * i, r = r0 + rl;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cl = tx + 16 * j, c = c0 + cl;
+      if (r < N && c < N) {
+        const size_t e = size_t(r) * N + c;
+        const double sv = ad[i][j] + df64_value(a[i][j]);
+        Sup[e] = sv;
+        if (!diag || rl <= cl) {
+          const double v = C != nullptr ? sv + C[e] : sv;
+          permd[slot[e]] = (r == c) ? v : 2.0 * v;
+        }
+      }
+    }
+  }
+}
+
+__global__ void piece_sum_d_kernel(int n_pieces, const int32_t* __restrict__ piece_start,
+                                   const int32_t* __restrict__ piece_class,
+                                   const double* __restrict__ permd,
+                                   const double* __restrict__ mult,
+                                   double* __restrict__ piece_buf, double* __restrict__ out) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pc >= n_pieces) return;
+  double s = 0.0;
+  for (int e = piece_start[pc]; e < piece_start[pc + 1]; ++e) s += permd[e];
+  const int cls = piece_class[pc];
+  if (cls >= 0)
+    out[cls] = s / mult[cls];
+  else
+    piece_buf[pc] = s;
+}
+
+void launch_spass_df(const ClassMap& cm, int N, int p, const float* Yh, const float* Yl,
+                     const double* C, const int32_t* slot, double* Sup, double* permd,
+                     const double* mult, double* piece_buf, double* y, cudaStream_t s) {
+  const int nt = (N + DT - 1) / DT;
+  const int grid = nt * (nt + 1) / 2;
+  count_launches(2);
+  spass_df_kernel<<<grid, 256, 0, s>>>(N, p, Yh, Yl, C, slot, Sup, permd);
+  piece_sum_d_kernel<<<(cm.n_pieces + 255) / 256, 256, 0, s>>>(
+      cm.n_pieces, cm.piece_start, cm.piece_class, permd, mult, piece_buf, y);
+  if (cm.n_multi > 0) {
+    count_launches(1);
+    class_finalize_df_kernel<<<(cm.n_multi + 255) / 256, 256, 0, s>>>(
+        cm.n_multi, cm.multi_class, cm.multi_range, piece_buf, mult, y);
+  }
   MDS_CUDA(cudaGetLastError());
 }
 

@@ -193,8 +193,9 @@ static int gemm32_cfg(int N, int ncol, const float* G, const float* U, const int
                       const float* w, float gscale, const float* Y, void* ws, size_t ws_bytes,
                       cudaStream_t s) {
   const int gx = (ncol + BN - 1) / BN, gy = (N + 127) / 128;
-  int splits = (2 * 152 + gx * gy - 1) / (gx * gy);
-  splits = std::min(splits, std::max(1, N / 128));
+  // about four blocks per SM (the kernel holds up to three per SM), each split >= 64 K-rows
+  int splits = (4 * 152 + gx * gy - 1) / (gx * gy);
+  splits = std::min(splits, std::max(1, N / 64));
   const size_t per = size_t(N) * ncol * sizeof(float);
   if (size_t(splits + 1) * per > ws_bytes) splits = int(ws_bytes / per) - 1;  // +1: YM slice
   if (splits < 1) throw DeviceError{cudaErrorMemoryAllocation};
