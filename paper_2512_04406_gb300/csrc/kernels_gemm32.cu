@@ -126,22 +126,22 @@ __global__ void __launch_bounds__(256) gemm32_kernel(int N, int ncol, int kchunk
 
 // out[r, c] = scale * sum_k (Y[r, k] M1[k, c] + Up[r, k] M2[k, c]) for the
 // Q(W) Y = Y (U'Y) + U (Y'Y) part of the Hessian (Proposition 4.2); M = [M1; M2]
-// (2p x p).  64 x 64 output tile per block, 4 x 4 per thread, K chunks of 16.
+// (2p x p).  32 x 64 output tile per block, 2 x 4 per thread, K chunks of 16.
 __global__ void __launch_bounds__(256) ym_kernel(int N, int p, const float* __restrict__ Y,
                                                  const float* __restrict__ Up,
                                                  const float* __restrict__ M, float scale,
                                                  float* __restrict__ out) {
-  __shared__ float As[16][65], Bs[16][64];
+  __shared__ float As[16][33], Bs[16][64];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-  float acc[4][4];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 64;
+  float acc[2][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
   const int K = 2 * p;  // k < p: Y with M1; k >= p: Up with M2
   for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int t = threadIdx.x; t < 64 * 16; t += 256) {
+    for (int t = threadIdx.x; t < 32 * 16; t += 256) {
       const int rr = t / 16, kk = t % 16;
       const int r = r0 + rr, k = k0 + kk;
       float v = 0.f;
@@ -156,20 +156,20 @@ __global__ void __launch_bounds__(256) ym_kernel(int N, int p, const float* __re
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
+      float a[2], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 2; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     const int r = r0 + ty + 16 * i;
     if (r >= N) continue;
 #pragma unroll
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) ym_kernel(int N, int p, const float* __re
 
 void launch_ym32(int N, int p, const float* Y, const float* Up, const float* M, float scale,
                  float* out, cudaStream_t s) {
-  dim3 grid((p + 63) / 64, (N + 63) / 64);
+  dim3 grid((p + 63) / 64, (N + 31) / 32);
   count_launches(1);
   ym_kernel<<<grid, 256, 0, s>>>(N, p, Y, Up, M, scale, out);
   MDS_CUDA(cudaGetLastError());

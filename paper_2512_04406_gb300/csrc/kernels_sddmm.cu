@@ -40,17 +40,36 @@ __global__ void __launch_bounds__(256) sddmm_tile_kernel(int N, int p, const flo
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < p; k0 += SKC) {
-    for (int t = threadIdx.x; t < ST * SKC; t += 256) {
+  // register prefetch of the next K chunk: each thread stages 4 elements of each array
+  constexpr int PER = ST * SKC / 256;  // 4
+  float pyr[PER], pur[PER], pyc[PER], puc[PER];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * 256;
       const int rr = t / SKC, kk = t % SKC;
       const int gr = r0 + rr, gc = c0 + rr, k = k0 + kk;
       const bool okr = gr < N && k < p, okc = gc < N && k < p;
-      Yr[rr][kk] = okr ? Y[size_t(gr) * p + k] : 0.f;
-      Ur[rr][kk] = okr ? U[size_t(gr) * p + k] : 0.f;
-      Yc[rr][kk] = okc ? Y[size_t(gc) * p + k] : 0.f;
-      Uc[rr][kk] = okc ? U[size_t(gc) * p + k] : 0.f;
+      pyr[q] = okr ? Y[size_t(gr) * p + k] : 0.f;
+      pur[q] = okr ? U[size_t(gr) * p + k] : 0.f;
+      pyc[q] = okc ? Y[size_t(gc) * p + k] : 0.f;
+      puc[q] = okc ? U[size_t(gc) * p + k] : 0.f;
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < p; k0 += SKC) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + q * 256;
+      const int rr = t / SKC, kk = t % SKC;
+      Yr[rr][kk] = pyr[q];
+      Ur[rr][kk] = pur[q];
+      Yc[rr][kk] = pyc[q];
+      Uc[rr][kk] = puc[q];
     }
     __syncthreads();
+    if (k0 + SKC < p) fetch(k0 + SKC);
 #pragma unroll
     for (int kk = 0; kk < SKC; ++kk) {
       float yr[4], ur[4], yc[4], uc[4];
@@ -69,7 +88,6 @@ __global__ void __launch_bounds__(256) sddmm_tile_kernel(int N, int p, const flo
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(yr[i], uc[j], fmaf(ur[i], yc[j], acc[i][j]));
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
