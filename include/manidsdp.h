@@ -234,6 +234,24 @@ int manidsdp_bqp_index_map(int32_t q, int32_t order, int32_t* N, int64_t* m, int
  * Q: host q x q symmetric FP64; c: host q FP64 (NULL = 0).  Section 3.1. */
 int manidsdp_bqp_rhs(int32_t q, int32_t order, const double* Q, const double* c, double* b);
 
+/*
+ * manidsdp_ucqp_index_map - host helper: the real second-order relaxation of a
+ * unit-modulus complex quadratic program min x*Qx + Re(c'x), |x_i| = 1, with real
+ * Q, c (Section 3.1, UCQP paragraph).  Basis: the Laurent exponents delta with
+ * ||delta||_1 <= 2 (x_i conj(x_i) = 1 removed), N = 2q^2 + 2q + 1, ordered by
+ * ||delta||_1 and then by the list of nonzero (index, value) pairs; the class of
+ * entry (b, g) is {beta - gamma, gamma - beta} (real moments of delta and -delta
+ * coincide), m = (q^4 + 2q^3 + 5q^2 + 4q + 3)/3 classes ordered the same way.
+ * Pass idx = NULL to query *N and *m only.  idx: host N x N int32 output.
+ */
+int manidsdp_ucqp_index_map(int32_t q, int32_t* N, int64_t* m, int32_t* idx);
+
+/* Right-hand side b (host, m FP64 output) of the UCQP relaxation: on the unit
+ * torus x*Qx = trace(Q) + sum_{i != j} Q_ij x^(e_j - e_i) and
+ * Re(c'x) = sum_i c_i (x^{e_i} + x^{-e_i}) / 2, each class collecting the
+ * coefficients of delta and -delta.  Q: host q x q real symmetric; c: host q or NULL. */
+int manidsdp_ucqp_rhs(int32_t q, const double* Q, const double* c, double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,7 @@ Per outer iteration k (Algorithm 1):
   9. if lambda_min(X) < 0 carry U = [0, V] (Theorem 4.5; Section 5.1);
   10. update the factorisation size p;
   11. sigma rule (Eq. (5.1)).
-Stop when eta_max = max(eta_p, eta_d, eta_g) <= tol (Section 6, Eq. (6.1)).
+Stop when eta_max = max(eta_p, eta_d, eta_g) <= tol (the stopping criterion of Section 6).
 
 Readings where the paper is silent (each also listed in the design notes):
   * Y^0: the printed Y^0 = 0 is not on N_p; we start from a caller-supplied

@@ -22,7 +22,8 @@ __all__ = [
     "manidsdp_subproblem_eval",
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
-    "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms",
+    "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms", "manidsdp_ucqp_index_map",
+    "manidsdp_ucqp_rhs",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -99,6 +100,9 @@ _sig = {
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int64), _P]),
     "manidsdp_bqp_rhs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "manidsdp_ucqp_index_map": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int64), _P]),
+    "manidsdp_ucqp_rhs": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -247,4 +251,27 @@ def manidsdp_bqp_rhs(q: int, Q, c=None, order: int = 2) -> np.ndarray:
     b = np.empty(m.value)
     _check(_lib.manidsdp_bqp_rhs(q, order, _ptr(Q), _ptr(c), _ptr(b, np.float64, True)),
            "manidsdp_bqp_rhs")
+    return b
+
+
+def manidsdp_ucqp_index_map(q: int):
+    """Returns (N, m, idx[N, N] int32) of the real second-order UCQP relaxation."""
+    N, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.manidsdp_ucqp_index_map(q, ctypes.byref(N), ctypes.byref(m), None),
+           "manidsdp_ucqp_index_map")
+    idx = np.empty((N.value, N.value), dtype=np.int32)
+    _check(_lib.manidsdp_ucqp_index_map(q, ctypes.byref(N), ctypes.byref(m),
+                                        _ptr(idx, np.int32, True)), "manidsdp_ucqp_index_map")
+    return N.value, m.value, idx
+
+
+def manidsdp_ucqp_rhs(q: int, Q, c=None) -> np.ndarray:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    N, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.manidsdp_ucqp_index_map(q, ctypes.byref(N), ctypes.byref(m), None),
+           "manidsdp_ucqp_rhs")
+    b = np.empty(m.value)
+    _check(_lib.manidsdp_ucqp_rhs(q, _ptr(Q), _ptr(c), _ptr(b, np.float64, True)),
+           "manidsdp_ucqp_rhs")
     return b

@@ -116,3 +116,148 @@ extern "C" int manidsdp_bqp_rhs(int32_t q, int32_t order, const double* Q, const
     for (int j = i + 1; j < q; ++j) b[k++] = Q[size_t(i) * q + j] + Q[size_t(j) * q + i];
   return MANIDSDP_OK;
 }
+
+// ---- real second-order UCQP relaxation (Section 3.1, UCQP paragraph) -----------------
+// A Laurent exponent with ||delta||_1 <= 4 has at most four nonzero entries.  Its key
+// packs (||delta||_1, then each nonzero (index, value) in increasing index, each as
+// ((index + 1) << 4) | (value + 4) in 12 bits, unused slots 0) into an integer whose
+// order is: degree first, then the lexicographic order of the (index, value) list.
+namespace {
+
+struct Laurent {
+  int n = 0;
+  int i[4] = {0, 0, 0, 0};
+  int v[4] = {0, 0, 0, 0};
+};
+
+uint64_t laurent_key(const Laurent& d) {
+  int l1 = 0;
+  for (int t = 0; t < d.n; ++t) l1 += d.v[t] < 0 ? -d.v[t] : d.v[t];
+  uint64_t k = uint64_t(l1);
+  for (int t = 0; t < 4; ++t) {
+    k <<= 12;
+    if (t < d.n) k |= (uint64_t(d.i[t] + 1) << 4) | uint64_t(d.v[t] + 4);
+  }
+  return k;
+}
+
+// beta - gamma, zeros dropped, sign fixed so that the first nonzero entry is positive
+Laurent laurent_class(const Laurent& b, const Laurent& g) {
+  Laurent o;
+  int ib = 0, ig = 0;
+  while (ib < b.n || ig < g.n) {
+    int idx, val;
+    if (ig >= g.n || (ib < b.n && b.i[ib] < g.i[ig])) {
+      idx = b.i[ib];
+      val = b.v[ib++];
+    } else if (ib >= b.n || g.i[ig] < b.i[ib]) {
+      idx = g.i[ig];
+      val = -g.v[ig++];
+    } else {
+      idx = b.i[ib];
+      val = b.v[ib++] - g.v[ig++];
+    }
+    if (val != 0) {
+      o.i[o.n] = idx;
+      o.v[o.n] = val;
+      ++o.n;
+    }
+  }
+  if (o.n > 0 && o.v[0] < 0)
+    for (int t = 0; t < o.n; ++t) o.v[t] = -o.v[t];
+  return o;
+}
+
+std::vector<Laurent> ucqp_basis(int q) {
+  std::vector<Laurent> B;
+  B.push_back(Laurent{});
+  for (int a = 0; a < q; ++a)
+    for (int v : {1, -1, 2, -2}) {
+      Laurent d;
+      d.n = 1;
+      d.i[0] = a;
+      d.v[0] = v;
+      B.push_back(d);
+    }
+  for (int a = 0; a < q; ++a)
+    for (int c = a + 1; c < q; ++c)
+      for (int s : {1, -1})
+        for (int t : {1, -1}) {
+          Laurent d;
+          d.n = 2;
+          d.i[0] = a;
+          d.v[0] = s;
+          d.i[1] = c;
+          d.v[1] = t;
+          B.push_back(d);
+        }
+  std::sort(B.begin(), B.end(),
+            [](const Laurent& x, const Laurent& y) { return laurent_key(x) < laurent_key(y); });
+  return B;
+}
+
+}  // namespace
+
+extern "C" int manidsdp_ucqp_index_map(int32_t q, int32_t* N_out, int64_t* m_out, int32_t* idx) {
+  if (q < 1 || q > 254 || N_out == nullptr || m_out == nullptr) return MANIDSDP_E_ARG;
+  const int64_t N = 2 * int64_t(q) * q + 2 * q + 1;
+  if (N > 65535) return MANIDSDP_E_ARG;
+  const int64_t q4 = int64_t(q) * q * q * q;
+  *N_out = int32_t(N);
+  *m_out = (q4 + 2 * int64_t(q) * q * q + 5 * int64_t(q) * q + 4 * q + 3) / 3;
+  if (idx == nullptr) return MANIDSDP_OK;
+  const std::vector<Laurent> B = ucqp_basis(q);
+  std::vector<uint64_t> keys(size_t(N) * N);
+  for (int64_t r = 0; r < N; ++r)
+    for (int64_t c = 0; c < N; ++c) keys[size_t(r) * N + c] = laurent_key(laurent_class(B[r], B[c]));
+  std::vector<uint64_t> uniq(keys);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  if (int64_t(uniq.size()) != *m_out) return MANIDSDP_E_ARG;
+  for (size_t e = 0; e < keys.size(); ++e)
+    idx[e] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), keys[e]) - uniq.begin());
+  return MANIDSDP_OK;
+}
+
+extern "C" int manidsdp_ucqp_rhs(int32_t q, const double* Q, const double* c, double* b) {
+  if (q < 1 || Q == nullptr || b == nullptr) return MANIDSDP_E_ARG;
+  int32_t N;
+  int64_t m;
+  int st = manidsdp_ucqp_index_map(q, &N, &m, nullptr);
+  if (st != MANIDSDP_OK) return st;
+  // class ranks of the few classes that carry coefficients: rebuild the sorted key list
+  const std::vector<Laurent> B = ucqp_basis(q);
+  std::vector<uint64_t> uniq;
+  uniq.reserve(size_t(m));
+  for (int32_t r = 0; r < N; ++r)
+    for (int32_t s = 0; s < N; ++s) uniq.push_back(laurent_key(laurent_class(B[r], B[s])));
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  auto rank_of = [&](const Laurent& d) {
+    return size_t(std::lower_bound(uniq.begin(), uniq.end(), laurent_key(d)) - uniq.begin());
+  };
+  for (int64_t a = 0; a < m; ++a) b[a] = 0.0;
+  double tr = 0.0;
+  for (int i = 0; i < q; ++i) tr += Q[size_t(i) * q + i];
+  b[rank_of(Laurent{})] = tr;  // x_i conj(x_i) = 1
+  for (int i = 0; i < q; ++i) {
+    Laurent d;
+    d.n = 1;
+    d.i[0] = i;
+    d.v[0] = 1;
+    b[rank_of(d)] += c ? c[i] : 0.0;  // Re(c_i x_i) = c_i (x_i + conj(x_i)) / 2
+  }
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      if (i == j) continue;
+      Laurent xj, xi;  // conj(x_i) Q_ij x_j = Q_ij x^(e_j - e_i)
+      xj.n = 1;
+      xj.i[0] = j;
+      xj.v[0] = 1;
+      xi.n = 1;
+      xi.i[0] = i;
+      xi.v[0] = 1;
+      b[rank_of(laurent_class(xj, xi))] += Q[size_t(i) * q + j];
+    }
+  return MANIDSDP_OK;
+}

@@ -69,3 +69,16 @@ def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
         mds.manidsdp_setup(N, m, bad, b)
     with pytest.raises(mds.ManidsdpError):  # a class with no entry: A A* singular
         mds.manidsdp_setup(N, m + 1, idx, np.zeros(m + 1))
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 5, 8])
+def test_ucqp_index_map_and_rhs_bit_exact_vs_oracle(q):
+    from oracle import ucqp
+    N, m, idx = mds.manidsdp_ucqp_index_map(q)
+    ref, classes = ucqp.index_map(q)
+    assert (N, m) == (ref.shape[0], len(classes))
+    assert np.array_equal(idx, ref)
+    rng = np.random.default_rng(q)
+    Q = rng.standard_normal((q, q)); Q = Q + Q.T
+    c = rng.standard_normal(q)
+    assert np.array_equal(mds.manidsdp_ucqp_rhs(q, Q, c), ucqp.rhs(q, Q, c, classes))

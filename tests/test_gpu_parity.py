@@ -143,3 +143,29 @@ def test_order1_relaxation_solve(torch):
     ref = om.solve(inst["prob"], gaussian_factor(inst["N"], 2, 5))
     assert rep.status == mds.OK and rep.eta_max <= 1e-8
     assert abs(rep.value - ref["value"]) <= 1e-9 * abs(ref["value"])
+
+
+@pytest.mark.parametrize("q,seed", [(3, 0), (4, 1)])
+def test_ucqp_order2_solve_matches_oracle(torch, q, seed):
+    """Real second-order UCQP relaxation (Section 3.1): the same hot path on a
+    Laurent-exponent index map."""
+    from oracle import ucqp
+    from oracle.moment import multiplicities
+    rng = np.random.default_rng(100 + seed)
+    Q = rng.standard_normal((q, q)); Q = Q + Q.T
+    c = rng.standard_normal(q)
+    N, m, idx = mds.manidsdp_ucqp_index_map(q)
+    b = mds.manidsdp_ucqp_rhs(q, Q, c)
+    ref_idx, classes = ucqp.index_map(q)
+    prob = om.make_problem(ref_idx, multiplicities(ref_idx, m), ucqp.rhs(q, Q, c, classes))
+    ctx = mds.manidsdp_setup(N, m, idx, b)
+    try:
+        Y0 = gaussian_factor(N, 2, seed)
+        rep, _ = mds.manidsdp_solve(ctx, Y0, 2)
+    finally:
+        mds.manidsdp_destroy(ctx)
+    ref = om.solve(prob, Y0)
+    assert rep.status == mds.OK and rep.eta_max <= 1e-8 and max(ref["eta"]) <= 1e-8
+    assert abs(rep.value - ref["value"]) <= 1e-9 * abs(ref["value"])
+    best = min(ucqp.objective(rng.uniform(-np.pi, np.pi, q), Q, c) for _ in range(2000))
+    assert rep.value <= best + 1e-8

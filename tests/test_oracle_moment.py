@@ -11,7 +11,7 @@ from oracle import moment, operators as ops
 
 
 def m_sos_closed_form(q):
-    # Eq. (3.4): m_sos^B = (q^4 - 2q^3 + 11q^2 + 14q + 24) / 24
+    # Section 3.1, BQP constraint count: m_sos^B = (q^4 - 2q^3 + 11q^2 + 14q + 24) / 24
     return (q**4 - 2 * q**3 + 11 * q**2 + 14 * q + 24) // 24
 
 
