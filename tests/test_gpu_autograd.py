@@ -100,8 +100,9 @@ def test_value_sensitivity_dV_dQ_finite_differences():
 def test_value_sensitivity_dV_dC_matches_dual_matrix():
     """dV/dC = Xt* + D: compared with the oracle's converged Xt + D, and with
     central differences of re-solved values.  A dense C moves the optimum off the
-    exact vertex (no residue dive; the solves stall near 1e-9), so h = 1e-3 and a
-    2e-3 relative check keep truncation and solve errors below the bound."""
+    exact vertex (no residue dive; the perturbed solves stall between 1e-9 and
+    1e-7), so h = 1e-2 and a 1e-3 relative check keep truncation (O(h^2)) and
+    solve errors below the bound."""
     torch_cuda()
     from paper_2512_04406_gb300.autograd import value_and_sensitivities
     from oracle import moment
@@ -117,7 +118,7 @@ def test_value_sensitivity_dV_dC_matches_dual_matrix():
     assert np.abs(XD - (ref["Xt"] + prob["D"])).max() <= 1e-6 * (1 + np.abs(XD).max())
     assert np.abs(y - ref["y"]).max() <= 1e-6
     rng = np.random.default_rng(3)
-    h = 1e-3
+    h = 1e-2
     prm.tol = 1e-9
     for _ in range(3):
         a, g_ = rng.choice(N, 2, replace=False)
@@ -128,9 +129,9 @@ def test_value_sensitivity_dV_dC_matches_dual_matrix():
                                      params=prm)
             try:
                 r, _ = mds.manidsdp_solve(ctx, gaussian_factor(N, 2, seed), 2)
-                assert r.eta_max <= 1e-8, r.as_dict()
+                assert r.eta_max <= 1e-6, r.as_dict()
                 vals.append(r.value)
             finally:
                 mds.manidsdp_destroy(ctx)
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(fd - 2 * XD[a, g_]) <= 2e-3 * max(1.0, abs(fd)), (fd, 2 * XD[a, g_])
+        assert abs(fd - 2 * XD[a, g_]) <= 1e-3 * max(1.0, abs(fd)), (fd, 2 * XD[a, g_])
