@@ -15,8 +15,11 @@ Readings where the paper is silent (each also listed in the design notes):
     Gaussian matrix with rows normalised.
   * Inner tolerance: RTR stops when ||grad|| <= eps_k with
     eps_k = max(tol_grad_min, min(tol_grad_max, tol_grad_factor * ||R^k|| / (1 + ||b||))),
-    eps_0 = tol_grad_max: the same scaled residual the sigma rule (5.1) weighs
-    against ||grad||, so the inner solve always has work while R is nonzero.
+    eps_0 = tol_grad_max, tol_grad_factor = 1: the same scaled residual the sigma
+    rule (5.1) weighs against ||grad||, so the inner solve always has work while R
+    is nonzero, and a subproblem solved to its tolerance leaves sigma unchanged
+    (a factor 0.1 made sigma double after every solved subproblem, stiffening the
+    quartic penalty until the trust region collapsed).
   * Rank update (the paper defers to ManiSDP, Section 5.1, not reproduced in the
     paper): after the multiplier update, directions of Y whose eigenvalue in
     Y'Y falls below rank_tol * lambda_max(Y'Y) are dropped (Y <- Y V_r, rows
@@ -48,7 +51,7 @@ DEFAULTS = dict(
     sigma0=1.0, sigma_min=1e-3, sigma_max=1e6, gamma=2.0, kappa1=0.1, kappa2=10.0,
     p0=2, p_min=2, p_max=256, delta_max=8,
     max_outer=300, max_rtr=200, max_tcg=500, tol=1e-8,
-    tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1e-1, tcg_floor=1e-10, tcg_abs=0.1,
+    tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1.0, tcg_floor=1e-10, tcg_abs=0.1,
     rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0,
     lanczos_k=300,
 )

@@ -499,7 +499,7 @@ void default_params(manidsdp_params* p) {
   p->tol = 1e-8;
   p->tol_grad_min = 1e-11;
   p->tol_grad_max = 1e-2;
-  p->tol_grad_factor = 0.1;
+  p->tol_grad_factor = 1.0;
   p->rank_tol = 1e-10;
   p->neg_tol = 1e-10;
   p->tcg_floor = 1e-10;
