@@ -165,7 +165,7 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
         Xt = Xt - sigma * R
         z = sp.rowdot((Xt + D) @ Y, Y)
         X = Xt + D - np.diag(z)
-        lam, V, lam_max = extreme_eigs(X, prm["delta_max"], eig, prm["lanczos_k"])
+        lam, V, lam_max = extreme_eigs(X, max(1, prm["delta_max"]), eig, prm["lanczos_k"])
         eta_p, eta_d, eta_g, pobj, dobj = kkt_residuals(prob, y, S, X, z, float(lam[0]), lam_max)
         eta = max(eta_p, eta_d, eta_g)
         if history is not None:
