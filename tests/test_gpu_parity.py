@@ -169,3 +169,19 @@ def test_ucqp_order2_solve_matches_oracle(torch, q, seed):
     assert abs(rep.value - ref["value"]) <= 1e-9 * abs(ref["value"])
     best = min(ucqp.objective(rng.uniform(-np.pi, np.pi, q), Q, c) for _ in range(2000))
     assert rep.value <= best + 1e-8
+
+
+@pytest.mark.parametrize("order,q,seed", [(1, 16, 1000), (1, 41, 1001), (1, 64, 1002),
+                                          (2, 6, 1003), (2, 10, 1004), (2, 14, 1005)])
+def test_small_instances_of_the_batched_mix(torch, order, q, seed):
+    """Instances shaped like the many-small-instances workload (order-1 relaxations
+    with n in [16, 64], order-2 with n in [6, 14], per-instance seeds), solved one by
+    one through the same path; value against the oracle and, for n <= 16, brute force."""
+    inst = instance(q, seed, order=order)
+    rep, _, _ = gpu_solve(torch, inst, 2, seed)
+    ref = om.solve(inst["prob"], gaussian_factor(inst["N"], 2, seed))
+    assert rep.status == mds.OK and rep.eta_max <= 1e-8 and max(ref["eta"]) <= 1e-8
+    assert abs(rep.value - ref["value"]) <= 1e-9 * abs(ref["value"])
+    if q <= 16:
+        fmin, _ = brute.bqp_min(inst["Q"], inst["c"])
+        assert rep.value <= fmin + 1e-8 * (1 + abs(fmin))
