@@ -80,6 +80,8 @@ typedef struct {
   double rank_tol, neg_tol, tcg_floor;
   double tcg_abs;         /* tCG also stops once ||r_j|| <= tcg_abs * eps_k */
   double carry_t0;        /* first step of the carried-direction line search; <= 0: sqrt(N) */
+  double round_eta;       /* try the rank-one rounding after outer iterations with
+                             eta_max <= round_eta (0 disables it) */
   int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 256 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */

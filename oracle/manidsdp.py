@@ -35,6 +35,13 @@ Readings where the paper is silent (each also listed in the design notes):
     that decreases Psi_{k+1} by at least 1e-4 t^2 |<U, Hess U>| / 2;
     otherwise drop the appended columns.
   * Eigenvectors are normalised to a positive first nonzero entry.
+  * Rank-one rounding (the locking discussion notes that an exact rounding step
+    turns near-locking into finite locking): after an outer iteration with
+    eta_max <= round_eta, round Y to Yr = sign(Y w) (N x 1, w the top eigenvector of
+    Y'Y).  If Yr Yr' is consistent with the classes (R = 0) and its certificate
+    X_r = Xt + D - Diag(diag((Xt + D) Yr Yr')) with the current multiplier has
+    lambda_min >= -tol (1 + |lambda_max|), the KKT residuals of (Yr, y_r, Xt) are
+    at rounding level and the solve stops there.
 """
 from __future__ import annotations
 
@@ -52,7 +59,7 @@ DEFAULTS = dict(
     p0=2, p_min=2, p_max=256, delta_max=8,
     max_outer=300, max_rtr=200, max_tcg=500, tol=1e-8,
     tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1.0, tcg_floor=1e-10, tcg_abs=0.1,
-    rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0,
+    rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0, round_eta=1e-2,
     lanczos_k=300,
 )
 
@@ -177,6 +184,29 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
                       lam_max=lam_max, totals=totals)
         if eta <= prm["tol"]:
             break
+        # rank-one rounding
+        if eta <= prm["round_eta"]:
+            w_, Wv_ = np.linalg.eigh(Y.T @ Y)
+            Yr = np.sign(Y @ Wv_[:, -1])[:, None]
+            Yr[Yr == 0] = 1.0
+            Sr = Yr @ Yr.T
+            yr = ops.y_of(Sr, C, idx, mult)
+            Rr = ops.Astar(yr, idx) - Sr - Cz
+            if np.abs(Rr).max() == 0.0:
+                zr = sp.rowdot((Xt + D) @ Yr, Yr)
+                Xr = Xt + D - np.diag(zr)
+                lr, _, lmaxr = extreme_eigs(Xr, 1, eig, prm["lanczos_k"])
+                er = kkt_residuals(prob, yr, Sr, Xr, zr, float(lr[0]), lmaxr)
+                if max(er[:3]) <= prm["tol"]:
+                    result = dict(Y=Yr, y=yr, Xt=Xt, z=zr, X=Xr, S=Sr, eta=er[:3], value=er[4],
+                                  pobj=er[3], outer=k + 1, p=1, sigma=sigma,
+                                  lam_min=float(lr[0]), lam_max=lmaxr, totals=totals,
+                                  rounded=True)
+                    if history is not None:
+                        history.append(dict(k=k, p=1, sigma=sigma, eta_p=er[0], eta_d=er[1],
+                                            eta_g=er[2], lam_min=float(lr[0]), gnorm=0.0, rtr=0,
+                                            hessvecs=0, dobj=er[4], rounded=True))
+                    break
         # step 10 (first half): drop numerically null directions of Y
         w, Wv = np.linalg.eigh(Y.T @ Y)
         keep = w > prm["rank_tol"] * w[-1]

@@ -388,7 +388,8 @@ struct LanczosOut {
 };
 
 // Lanczos with full reorthogonalisation on X = XD - Diag(z) (z on device).
-LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
+LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
+                   bool want_vecs = true) {
   const int N = c->N;
   double t_lz = 0.0;
   if (c->prm.profile) {
@@ -462,7 +463,7 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
   }
   // Ritz vectors into Vn (row-major N x ns): column i = sum_j s_i[j] v_j
   std::vector<double> neg(kk);
-  for (int i = 0; i < ns; ++i) {
+  for (int i = 0; i < (want_vecs ? ns : 0); ++i) {
     for (int j = 0; j < kk; ++j) neg[j] = -svecs[i][j];
     MDS_CUDA(cudaMemcpyAsync(c->lh, neg.data(), kk * sizeof(double), cudaMemcpyHostToDevice, c->s));
     MDS_CUDA(cudaMemsetAsync(c->lw, 0, N * sizeof(double), c->s));
@@ -481,7 +482,7 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small) {
     launch_axpby(N, sgn, c->lw, 0.0, nullptr, c->ls, c->s);
     launch_set_cols(N, ns, i, 1, c->ls, c->Vn, c->s);
   }
-  out.nvec = ns;
+  out.nvec = want_vecs ? ns : 0;
   sync(c);
   if (t_lz < 0.0)
     c->ms_lz += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
@@ -505,6 +506,7 @@ void default_params(manidsdp_params* p) {
   p->tcg_floor = 1e-10;
   p->tcg_abs = 0.1;
   p->carry_t0 = 0.0;
+  p->round_eta = 1e-2;
   p->p0 = 2;
   p->p_min = 2;
   p->p_max = 256;
@@ -1240,6 +1242,51 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
         MDS_CUDA(cudaMemcpyAsync(A.data(), c->M2, A.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
         sync(c);
         HostEig e = jacobi_eig(A, p);
+        // rank-one rounding: Yr = sign(Y w), w the top eigenvector of Y'Y; accept when
+        // Yr Yr' is consistent with the classes (R = 0) and its certificate is PSD
+        if (eta <= P.round_eta) {
+          std::vector<double> wtop(p);
+          for (int i = 0; i < p; ++i) wtop[i] = e.V[i + size_t(p) * (p - 1)];
+          MDS_CUDA(cudaMemcpyAsync(c->M1, wtop.data(), p * sizeof(double), cudaMemcpyHostToDevice, c->s));
+          launch_gemm<double>(N, 1, p, c->Y, p, c->M1, 1, c->GY, 1, 1.0, 0.0, nullptr, nullptr,
+                              0.0, nullptr, c->gws, c->gws_bytes, c->s);
+          launch_sign(N, c->GY, c->Yt, c->s);
+          double fr, r2r;
+          const bool mx = mixed(c);
+          evaluate(c, c->Yt, 1, c->yt, mx ? nullptr : c->Gt, nullptr, &fr, &r2r,
+                   mx ? c->Gth : nullptr, mx ? c->Gtl : nullptr);
+          if (r2r == 0.0) {
+            launch_gemm<double>(N, 1, N, c->XD, N, c->Yt, 1, c->GY, 1, 1.0, 0.0, nullptr, nullptr,
+                                0.0, nullptr, c->gws, c->gws_bytes, c->s);
+            launch_rowdot(N, 1, c->GY, c->Yt, c->zt, c->s);
+            LanczosOut lr = lanczos(c, c->zt, P.lanczos_k, 1, false);
+            double byr;
+            dots(c, c->m, 1, c->b, c->yt, &byr);
+            const double ed = std::max(0.0, -lr.lo[0]) / (1.0 + std::fabs(lr.hi));
+            // with R = 0 the evaluated Psi is <Xt + D, S_r + C> = sum(z_r) + <C, Xt + D>
+            const double po = fr;
+            const double eg = std::fabs(po - byr) / (1.0 + std::fabs(po) + std::fabs(byr));
+            if (std::max(ed, eg) <= P.tol) {
+              MDS_CUDA(cudaMemcpyAsync(c->Y, c->Yt, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+              MDS_CUDA(cudaMemcpyAsync(c->y, c->yt, c->m * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+              MDS_CUDA(cudaMemcpyAsync(c->z, c->zt, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+              p = 1;
+              rep.eta_p = 0.0;
+              rep.eta_d = ed;
+              rep.eta_g = eg;
+              rep.pobj = po;
+              rep.value = byr;
+              rep.lambda_min = lr.lo[0];
+              rep.lambda_max = lr.hi;
+              rep.p = 1;
+              if (P.verbose)
+                std::fprintf(stderr, "[manidsdp] k=%d rank-one rounding accepted: eta=(0 %.2e %.2e) V=%.12f\n",
+                             k, ed, eg, byr);
+              status = MANIDSDP_OK;
+              break;
+            }
+          }
+        }
         const double wmax = e.w[p - 1];
         std::vector<int> keep;
         for (int i = 0; i < p; ++i)

@@ -188,6 +188,8 @@ void launch_basis_update(int N, int k, const double* V, const double* h, double*
 // Copy N x p_old into N x p_new (zero-padding new columns) or select columns via a p_old x p_new
 // matrix (out = A W) - via launch_gemm.
 void launch_pad_cols(int N, int p_old, int p_new, const double* in, double* out, cudaStream_t s);
+// out[i] = +1 if u[i] >= 0 else -1
+void launch_sign(int n, const double* u, double* out, cudaStream_t s);
 void launch_set_cols(int N, int p, int c0, int nc, const double* src /*N x nc*/, double* out,
                      cudaStream_t s);
 

@@ -708,6 +708,16 @@ void launch_basis_update(int N, int k, const double* V, const double* h, double*
   MDS_CUDA(cudaGetLastError());
 }
 
+__global__ void sign_kernel(int n, const double* __restrict__ u, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = u[i] < 0.0 ? -1.0 : 1.0;
+}
+void launch_sign(int n, const double* u, double* out, cudaStream_t s) {
+  count_launches(1);
+  sign_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, u, out);
+  MDS_CUDA(cudaGetLastError());
+}
+
 __global__ void pad_cols_kernel(int N, int p_old, int p_new, const double* __restrict__ in,
                                 double* __restrict__ out) {
   const size_t n = size_t(N) * p_new;
