@@ -6,19 +6,27 @@ min x'Qx + c'x over x in {-1,1}^80 (Section 6.1): moment matrix 3241 x 3241,
 1,666,981 classes (monomials of degree <= 4), Q and c iid N(0,1) from seed 0,
 p_0 = ceil(ln m) = 15 (Section 6.1 sets p_0 = ceil(log m)).
 
-A step is one full solve (Algorithm 1: every RTR iteration, Hessian-vector
-product, multiplier update and Lanczos run) from the seeded start to
-eta_max <= 1e-8 with the mixed-precision form (FP32 Hessian-vector products,
-FP64 cost, gradient, multiplier, KKT residuals and Lanczos).  Inputs sit in HBM
-before the timed region; the working set (index map 42 MB, three N x N FP64
-matrices 252 MB) exceeds the 129 MB L2, so no flush is needed between steps.
+A step is one pass of the whole hot path: one ALM outer iteration of Algorithm 1
+(the RTR solve of the subproblem with its tCG Hessian-vector products, the
+multiplier update, the Lanczos certificate check, the rank and sigma updates), in
+the mixed-precision form (FP32 Hessian-vector products, df64 cost and gradient,
+FP64 multiplier, KKT residuals and Lanczos).  The W warm-up steps are the first W
+outer iterations of a fresh solve from the seeded start; the K timed steps are
+the next K outer iterations of the same solve (warm start: factor, multiplier
+and penalty carried over).  Inputs sit in HBM before the timed region; the
+working set (index map 42 MB, N x N FP64 multiplier and G 168 MB) exceeds the
+129 MB L2, so no flush is needed between steps.  Beside the headline the line
+reports a full solve to eta_max <= 1e-8 of the q = 60 instance (N = 1831) and
+the same q = 40 instance solved by the mixed and by the plain FP64 form.
 
-Under torchrun (N > 1) each rank solves its own replica (the single-instance
-path has no exchange step on one GPU); value = total solves / max-over-ranks time.
+Under torchrun (N > 1) each rank runs its own replica (the single-instance path
+has no exchange step); value = max-over-ranks time / (K x ranks), the job's time
+per outer iteration.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload and projects the full-solve time from the GPU
-solve's operation counts (see the JSON's cpu_baseline.sample).
+sample of the same workload (its Hessian-vector product, cost-plus-gradient
+evaluation and certificate matvec) and scales it to one outer iteration by the
+operation counts of an outer iteration (see the JSON's cpu_baseline.sample).
 """
 from __future__ import annotations
 
@@ -39,18 +47,19 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "solve time to KKT≤1e-8 (mixed vs FP64 GPU); Hess-vec GB/s or TC % of roofline"
-UNIT = "s/solve"
+UNIT = "s/ALM-outer-iteration"
 
-# Operation counts of one mixed-precision solve of this workload, used to scale
-# the sampled oracle timings to a full solve when no GPU run precedes them.
-# bench.py overwrites them with the counts of its own GPU solve when it has one.
-DEFAULT_COUNTS = dict(hessvecs=3000, evals=600, grads=450, lanczos_matvecs=6000, p=16)
+# Operation counts of one outer iteration of this workload (means over the timed
+# steps of a GPU run), used to scale the sampled oracle timings to one outer
+# iteration when no GPU run precedes them.  The GPU arm uses the counts of its
+# own timed steps.
+DEFAULT_COUNTS = dict(hessvecs=400, evals=40, grads=30, lanczos_matvecs=300, p=100)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--q", type=int, default=80)
@@ -60,6 +69,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--hv-reps", type=int, default=30)
+    ap.add_argument("--solve-q", type=int, default=60,
+                    help="instance size of the full solve reported beside the headline (0 skips)")
+    ap.add_argument("--compare-q", type=int, default=40,
+                    help="instance size for the mixed-vs-FP64 solve comparison (0 skips it)")
     ap.add_argument("--hv-only", type=int, default=0,
                     help="only time the Hessian-vector product at this p (profiling)")
     return ap.parse_args()
@@ -177,7 +190,7 @@ def measure_hessvec(mds, torch, ctx, N, p, reps, precision, seed=11):
 def cpu_baseline(q, seed, counts, budget_s):
     """The FP64 oracle, as it stands, on this host: time its Hessian-vector
     product, cost-plus-gradient evaluation and certificate matvec at the
-    workload's size, then scale by the GPU solve's operation counts."""
+    workload's size, then scale by the operation counts of one outer iteration."""
     from oracle import manidsdp as om, moment, operators as ops, subproblem as sp
     from synthetic import bqp_instance, gaussian_factor
     t_setup = time.perf_counter()
@@ -212,9 +225,9 @@ def cpu_baseline(q, seed, counts, budget_s):
         "value": proj, "unit": UNIT, "cores": cores, "kind": "oracle",
         "sample": (f"oracle FP64 at q={q} (N={N}, m={m}, p={p}): {len(t_hv)} Hessian-vector products "
                    f"({hv:.3f} s each), {len(t_ev)} cost+gradient evaluations ({ev:.3f} s), "
-                   f"{10 * len(t_mv)} certificate matvecs ({mv * 1e3:.1f} ms); value projects a full "
-                   f"solve from the GPU solve's counts (hessvecs={counts['hessvecs']}, "
-                   f"evals={counts['evals']}, lanczos matvecs={counts['lanczos_matvecs']}); "
+                   f"{10 * len(t_mv)} certificate matvecs ({mv * 1e3:.1f} ms); value projects one "
+                   f"outer iteration from its counts (hessvecs={counts['hessvecs']:.0f}, "
+                   f"evals={counts['evals']:.0f}, lanczos matvecs={counts['lanczos_matvecs']:.0f}); "
                    f"index-map setup {t_setup:.1f} s not included"),
     }
 
@@ -279,8 +292,14 @@ def main():
         mds.manidsdp_destroy(ctx)
         return
     Y0 = torch.tensor(gaussian_factor(N, p0, args.seed + rank), device="cuda")
-    for _ in range(args.warmup):
-        mds.manidsdp_solve(ctx, Y0, p0)
+    # warm-up: the first W outer iterations of a fresh solve
+    prm.max_outer = args.warmup
+    prm.warm_start = 0
+    mds.manidsdp_set_params(ctx, prm)
+    rep_w, _ = mds.manidsdp_solve(ctx, Y0, p0)
+    prm.max_outer = args.steps
+    prm.warm_start = 1
+    mds.manidsdp_set_params(ctx, prm)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -288,11 +307,8 @@ def main():
     clocks.start()
     l0 = mds.manidsdp_launch_count()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    reps = []
     e0.record(stream)
-    for _ in range(args.steps):
-        rep, p_fin = mds.manidsdp_solve(ctx, Y0, p0)
-        reps.append(rep)
+    rep, p_fin = mds.manidsdp_solve(ctx, Y0, p0)
     e1.record(stream)
     torch.cuda.synchronize()
     launches = mds.manidsdp_launch_count() - l0
@@ -302,9 +318,8 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     clk = clocks.stop()
-    rep = reps[-1]
-    ok = all(r.status == mds.OK and r.eta_max <= 1e-8 for r in reps)
-    value = ms / 1e3 / (args.steps * world)
+    steps_done = max(1, rep.outer)
+    value = ms / 1e3 / (steps_done * world)
 
     # dominant kernel: the Hessian-vector product, live (phase events inside the
     # timed solves) and in isolation at p = p_0
@@ -341,44 +356,91 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        # the user's call: host index map and b, host start, host outputs
+        # the user's call from host memory: setup from the host index map and b, a
+        # solve of W + K outer iterations from a host start, host outputs
+        pe = mds.manidsdp_default_params()
+        pe.precision_mode = prec
+        pe.max_outer = args.warmup + args.steps
         y_host = np.empty(m)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx2 = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
+        ctx2 = mds.manidsdp_setup(N, m, idx, b, params=pe, stream=stream.cuda_stream)
         Y0h = gaussian_factor(N, p0, args.seed + rank)
-        Yout = np.empty(N * prm.p_max)
+        Yout = np.empty(N * pe.p_max)
         rep2, p2 = mds.manidsdp_solve(ctx2, Y0h, p0, Y_out=Yout, y_out=y_host)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         mds.manidsdp_destroy(ctx2)
-        e2e = {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(idx.nbytes + b.nbytes + Y0h.nbytes),
-               "d2h_bytes_per_step": int(y_host.nbytes + N * p2 * 8),
-               "includes": "setup (index-map validation, inverse map, H2D) + solve + D2H of y and Y"}
+        e2e = {"value": t_e2e / max(1, rep2.outer), "unit": UNIT,
+               "h2d_bytes_per_step": int((idx.nbytes + b.nbytes + Y0h.nbytes) / max(1, rep2.outer)),
+               "d2h_bytes_per_step": int((y_host.nbytes + N * p2 * 8) / max(1, rep2.outer)),
+               "includes": f"setup (index-map validation, inverse map, H2D) + {rep2.outer} outer "
+                           "iterations from a host start + D2H of y and Y, per outer iteration"}
+
+    solve60 = None
+    if rank == 0 and args.solve_q > 0:
+        Qs, cs, Ns, ms_, idxs, bs, p0s = workload(args.solve_q, args.seed)
+        ps = mds.manidsdp_default_params()
+        ps.precision_mode = prec
+        cs_ = mds.manidsdp_setup(Ns, ms_, idxs, bs, params=ps, stream=stream.cuda_stream)
+        Y0s = torch.tensor(gaussian_factor(Ns, p0s, args.seed), device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs, _ = mds.manidsdp_solve(cs_, Y0s, p0s)
+        torch.cuda.synchronize()
+        solve60 = {"q": args.solve_q, "N": Ns, "m": ms_, "s": time.perf_counter() - t0,
+                   "eta_max": rs.eta_max, "value": rs.value, "outer": rs.outer,
+                   "hessvecs": rs.hessvecs, "converged": rs.status == mds.OK}
+        mds.manidsdp_destroy(cs_)
+
+    compare = None
+    if rank == 0 and args.compare_q > 0:
+        # the same instance solved by the mixed form and by the plain FP64 form
+        Qc, cc_, Nc, mc, idxc, bc, p0c = workload(args.compare_q, args.seed)
+        Y0c = torch.tensor(gaussian_factor(Nc, p0c, args.seed), device="cuda")
+        compare = {"q": args.compare_q, "N": Nc}
+        for name, pm in (("mixed", mds.PREC_MIXED), ("fp64", mds.PREC_FP64)):
+            pc = mds.manidsdp_default_params()
+            pc.precision_mode = pm
+            cx = mds.manidsdp_setup(Nc, mc, idxc, bc, params=pc, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, _ = mds.manidsdp_solve(cx, Y0c, p0c)
+            torch.cuda.synchronize()
+            compare[name] = {"s": time.perf_counter() - t0, "eta_max": rc.eta_max,
+                             "value": rc.value, "outer": rc.outer, "hessvecs": rc.hessvecs}
+            mds.manidsdp_destroy(cx)
+        compare["speedup_mixed_over_fp64"] = compare["fp64"]["s"] / compare["mixed"]["s"]
+        compare["value_rel_diff"] = abs(compare["fp64"]["value"] - compare["mixed"]["value"]) / abs(
+            compare["fp64"]["value"])
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        counts = dict(hessvecs=rep.hessvecs, evals=rep.evals, grads=rep.grads,
-                      lanczos_matvecs=rep.lanczos_matvecs, p=p_avg)
+        counts = dict(hessvecs=rep.hessvecs / steps_done, evals=rep.evals / steps_done,
+                      grads=rep.grads / steps_done, lanczos_matvecs=rep.lanczos_matvecs / steps_done,
+                      p=p_avg)
         cb = cpu_baseline(args.q, args.seed, counts, args.cpu_sample_s)
 
     mds.manidsdp_destroy(ctx)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
+            "warmup": args.warmup, "ms_per_step": ms / steps_done, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/f64 (FP32 Hessian-vector products, FP64 elsewhere)" if prec == mds.PREC_MIXED else "f64",
             "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
             "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
                        "N": N, "m": m, "p0": p0, "precision": args.precision,
-                       "l2": "working set > L2 (idx 42 MB + 3 x 84 MB N x N FP64), no flush",
+                       "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
+                       "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",
                        "parallelism": f"replicas{world}"},
-            "converged": ok, "eta_max": rep.eta_max, "value_bound": rep.value, "outer": rep.outer,
+            "steps_done": steps_done, "eta_max_after": rep.eta_max, "value_after": rep.value,
+            "outer_total": args.warmup + rep.outer, "full_solve": solve60,
             "rtr_iters": rep.rtr_iters, "hessvecs": rep.hessvecs, "p_final": rep.p,
             "phase_ms": {"hessvec": rep.ms_hessvec, "eval": rep.ms_eval, "grad": rep.ms_grad,
                          "lanczos_wall": rep.ms_lanczos},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+            "mixed_vs_fp64": compare,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

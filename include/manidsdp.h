@@ -91,7 +91,10 @@ typedef struct {
                              stream (fills the ms_* fields of the report) */
   int32_t tcg_device;     /* 1 (default): each tCG run is one CUDA-graph launch whose
                              WHILE node loops on the device; 0: host-driven loop */
-  int32_t reserved;
+  int32_t warm_start;     /* 1: manidsdp_solve resumes from the context's factor,
+                             multiplier, sigma and inner-tolerance scale left by the
+                             previous solve (Y0/p0 ignored; the carried direction is not
+                             kept); 0 (default): start from Y0 with Xt = 0, sigma0 */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */
@@ -149,6 +152,11 @@ int manidsdp_setup(manidsdp_ctx** ctx, int32_t N, int64_t m, const int32_t* idx,
 
 /* Release every resource of the context (NULL is a no-op). */
 void manidsdp_destroy(manidsdp_ctx* ctx);
+
+/* Replace the parameters of a context.  p_max and precision_mode size the
+ * context's buffers and must equal the values given to manidsdp_setup; the Krylov
+ * cap cannot grow beyond the setup value.  E_ARG otherwise (nothing changed). */
+int manidsdp_set_params(manidsdp_ctx* ctx, const manidsdp_params* params);
 
 /* Replace the ALM state: multiplier Xt (host or device N x N FP64, NULL = zero)
  * and penalty sigma.  Section 3, Algorithm 0. */

@@ -18,7 +18,8 @@ from .build import LIB as _LIB_PATH
 __all__ = [
     "ManidsdpError", "Params", "Report", "Context",
     "manidsdp_default_params", "manidsdp_strerror", "manidsdp_setup", "manidsdp_destroy",
-    "manidsdp_set_state", "manidsdp_get_multiplier", "manidsdp_get_dual_matrix",
+    "manidsdp_set_state", "manidsdp_set_params", "manidsdp_get_multiplier",
+    "manidsdp_get_dual_matrix",
     "manidsdp_subproblem_eval",
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
@@ -49,7 +50,7 @@ class Params(ctypes.Structure):
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
             "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile", "tcg_device",
-            "reserved")]
+            "warm_start")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,6 +87,7 @@ _sig = {
                                       _P, ctypes.c_int32, _P, ctypes.POINTER(Params), _P]),
     "manidsdp_destroy": (None, [Context]),
     "manidsdp_set_state": (ctypes.c_int, [Context, _P, ctypes.c_double]),
+    "manidsdp_set_params": (ctypes.c_int, [Context, ctypes.POINTER(Params)]),
     "manidsdp_get_multiplier": (ctypes.c_int, [Context, _P]),
     "manidsdp_get_dual_matrix": (ctypes.c_int, [Context, _P]),
     "manidsdp_subproblem_eval": (ctypes.c_int, [Context, _P, ctypes.c_int32, _dp, _P, _P, _P,
@@ -176,6 +178,10 @@ def manidsdp_setup(N: int, m: int, idx, b, c_kind: int = C_ZERO, c_dense=None,
 
 def manidsdp_destroy(ctx: Context) -> None:
     _lib.manidsdp_destroy(ctx)
+
+
+def manidsdp_set_params(ctx: Context, params: Params) -> None:
+    _check(_lib.manidsdp_set_params(ctx, ctypes.byref(params)), "manidsdp_set_params")
 
 
 def manidsdp_set_state(ctx: Context, Xt=None, sigma: float = 1.0) -> None:

@@ -209,6 +209,13 @@ struct manidsdp_ctx {
   int eval_p = 0;
   bool eval_ok = false;
   double psi = 0.0, r2 = 0.0;
+  // state kept for a warm-started (resumed) solve
+  bool resume_valid = false;
+  int resume_p = 0;
+  double resume_rscale = -1.0;
+  int resume_outer = 0;
+  bool resume_have_U = false;  // the last iteration augmented Y = [Y, 0] and set U = [0, V]
+  int resume_U_cols = 0;
   // counters and phase timers
   int hessvecs = 0, rtr_iters = 0, lanczos_mv = 0, evals = 0, grads = 0;
   double hv_psum = 0.0;
@@ -507,6 +514,7 @@ void default_params(manidsdp_params* p) {
   p->tcg_abs = 0.1;
   p->carry_t0 = 0.0;
   p->round_eta = 1e-2;
+  p->warm_start = 0;
   p->p0 = 2;
   p->p_min = 2;
   p->p_max = 256;
@@ -794,6 +802,16 @@ void manidsdp_destroy(manidsdp_ctx* ctx) {
   cudaStreamSynchronize(ctx->s);
   release(ctx);
   delete ctx;
+}
+
+int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
+  if (c == nullptr || prm == nullptr || prm->p_max != c->prm.p_max || prm->p0 < 1 ||
+      prm->p0 > prm->p_max || prm->p_min < 1 || prm->delta_max < 0 || prm->lanczos_k < 1 ||
+      prm->precision_mode != c->prm.precision_mode)
+    return MANIDSDP_E_ARG;
+  c->prm = *prm;
+  c->kmax = std::min(std::max(c->prm.lanczos_k, 1), std::min(c->kmax, c->N));
+  return MANIDSDP_OK;
 }
 
 int manidsdp_set_state(manidsdp_ctx* c, const double* Xt, double sigma) {
@@ -1139,14 +1157,23 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     const manidsdp_params& P = c->prm;
     c->hessvecs = c->rtr_iters = c->lanczos_mv = c->evals = c->grads = 0;
     c->hv_psum = c->ms_hv = c->ms_eval = c->ms_grad = c->ms_lz = 0.0;
-    set_state(c, nullptr, P.sigma0);
+    const bool resume = P.warm_start && c->resume_valid;
     int p = p0;
-    MDS_CUDA(cudaMemcpyAsync(c->tmp, Y0, size_t(N) * p * sizeof(double), cudaMemcpyDefault, c->s));
-    launch_retract(N, p, c->tmp, c->tmp, 0.0, c->Y, c->s);
-    bool have_U = false;
-    int U_cols = 0;
     double rscale = -1.0;
     double sigma = P.sigma0;
+    if (resume) {  // continue from the context's factor, multiplier and penalty
+      p = c->resume_p;
+      rscale = c->resume_rscale;
+      sigma = c->sigma;
+      c->eval_ok = false;
+    } else {
+      set_state(c, nullptr, P.sigma0);
+      c->resume_outer = 0;
+      MDS_CUDA(cudaMemcpyAsync(c->tmp, Y0, size_t(N) * p * sizeof(double), cudaMemcpyDefault, c->s));
+      launch_retract(N, p, c->tmp, c->tmp, 0.0, c->Y, c->s);
+    }
+    bool have_U = resume && c->resume_have_U;
+    int U_cols = have_U ? c->resume_U_cols : 0;
     for (int k = 0; k < P.max_outer; ++k) {
       c->sigma = sigma;
       // step 3a: the carried direction U = [0, V]
@@ -1327,6 +1354,12 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       }
     }
     c->sigma = sigma;
+    c->resume_valid = true;
+    c->resume_p = rep.p > 0 ? rep.p : p;
+    c->resume_rscale = rscale;
+    c->resume_outer += rep.outer;
+    c->resume_have_U = have_U;
+    c->resume_U_cols = U_cols;
     rep.rtr_iters = c->rtr_iters;
     rep.hessvecs = c->hessvecs;
     rep.lanczos_matvecs = c->lanczos_mv;

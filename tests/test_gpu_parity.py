@@ -185,3 +185,25 @@ def test_small_instances_of_the_batched_mix(torch, order, q, seed):
     if q <= 16:
         fmin, _ = brute.bqp_min(inst["Q"], inst["c"])
         assert rep.value <= fmin + 1e-8 * (1 + abs(fmin))
+
+
+def test_solve_resumes_from_context_state(torch):
+    """A solve stopped after two outer iterations and resumed with warm_start
+    (factor, multiplier, sigma kept in the context) reaches the oracle's value."""
+    inst = instance(10, 3)
+    prm = mds.manidsdp_default_params()
+    prm.max_outer = 2
+    ctx = make_ctx(inst, prm)
+    try:
+        Y0 = gaussian_factor(inst["N"], 2, 3)
+        rep1, _ = mds.manidsdp_solve(ctx, Y0, 2)
+        assert rep1.outer == 2
+        prm.warm_start = 1
+        prm.max_outer = 300
+        mds.manidsdp_set_params(ctx, prm)
+        rep2, _ = mds.manidsdp_solve(ctx, Y0, 2)
+    finally:
+        mds.manidsdp_destroy(ctx)
+    ref = om.solve(inst["prob"], gaussian_factor(inst["N"], 2, 3))
+    assert rep2.status == mds.OK and rep2.eta_max <= 1e-8
+    assert abs(rep2.value - ref["value"]) <= 1e-9 * abs(ref["value"])
