@@ -92,9 +92,10 @@ typedef struct {
   int32_t tcg_device;     /* 1 (default): each tCG run is one CUDA-graph launch whose
                              WHILE node loops on the device; 0: host-driven loop */
   int32_t warm_start;     /* 1: manidsdp_solve resumes from the context's factor,
-                             multiplier, sigma and inner-tolerance scale left by the
-                             previous solve (Y0/p0 ignored; the carried direction is not
-                             kept); 0 (default): start from Y0 with Xt = 0, sigma0 */
+                             multiplier, sigma, inner-tolerance scale and carried
+                             negative-curvature direction left by the previous solve
+                             (Y0/p0 ignored; a fresh start when no solve ran yet);
+                             0 (default): start from Y0 with Xt = 0, sigma0 */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */
@@ -221,7 +222,9 @@ int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t whic
  *   y_out  m FP64 (y at the final S);   z_out N FP64;
  *   Xt_out N x N FP64 final multiplier; report: host struct.
  * Returns MANIDSDP_OK when eta_max <= tol, MANIDSDP_E_NOCONV otherwise.
- * The context's multiplier and sigma are reset to 0 and params.sigma0 at entry.
+ * The context's multiplier and sigma are reset to 0 and params.sigma0 at entry,
+ * unless params.warm_start = 1 continues the previous solve on this context.
+ * The report's counters and phase times cover this call only.
  */
 int manidsdp_solve(manidsdp_ctx* ctx, const double* Y0, int32_t p0, double* Y_out,
                    int32_t* p_out, double* y_out, double* z_out, double* Xt_out,

@@ -1355,7 +1355,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     }
     c->sigma = sigma;
     c->resume_valid = true;
-    c->resume_p = rep.p > 0 ? rep.p : p;
+    c->resume_p = p;  // columns of c->Y now (after rank drop and augmentation)
     c->resume_rscale = rscale;
     c->resume_outer += rep.outer;
     c->resume_have_U = have_U;

@@ -187,23 +187,41 @@ def test_small_instances_of_the_batched_mix(torch, order, q, seed):
         assert rep.value <= fmin + 1e-8 * (1 + abs(fmin))
 
 
-def test_solve_resumes_from_context_state(torch):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_resumes_from_context_state(torch, prec):
     """A solve stopped after two outer iterations and resumed with warm_start
-    (factor, multiplier, sigma kept in the context) reaches the oracle's value."""
-    inst = instance(10, 3)
-    prm = mds.manidsdp_default_params()
-    prm.max_outer = 2
-    ctx = make_ctx(inst, prm)
+    (factor with its current column count, multiplier, sigma, inner-tolerance
+    scale and carried direction kept in the context) follows the uninterrupted
+    solve's trajectory exactly, and the resumed solve reaches the oracle's value."""
+    inst = instance(12, 3)
+    pm = mds.PREC_FP64 if prec == "fp64" else mds.PREC_MIXED
+    Y0 = gaussian_factor(inst["N"], 2, 3)
+
+    def params(max_outer, warm):
+        prm = mds.manidsdp_default_params()
+        prm.precision_mode = pm
+        prm.max_outer = max_outer
+        prm.warm_start = warm
+        return prm
+
+    ctx = make_ctx(inst, params(5, 0))
     try:
-        Y0 = gaussian_factor(inst["N"], 2, 3)
-        rep1, _ = mds.manidsdp_solve(ctx, Y0, 2)
-        assert rep1.outer == 2
-        prm.warm_start = 1
-        prm.max_outer = 300
-        mds.manidsdp_set_params(ctx, prm)
-        rep2, _ = mds.manidsdp_solve(ctx, Y0, 2)
+        whole, p_whole = mds.manidsdp_solve(ctx, Y0, 2)
     finally:
         mds.manidsdp_destroy(ctx)
+    ctx = make_ctx(inst, params(2, 0))
+    try:
+        rep1, p1 = mds.manidsdp_solve(ctx, Y0, 2)
+        assert rep1.outer == 2
+        mds.manidsdp_set_params(ctx, params(3, 1))
+        rep2, p2 = mds.manidsdp_solve(ctx, Y0, 2)
+        mds.manidsdp_set_params(ctx, params(300, 1))
+        rep3, _ = mds.manidsdp_solve(ctx, Y0, 2)
+    finally:
+        mds.manidsdp_destroy(ctx)
+    if whole.outer == 5:  # not converged inside the first five iterations
+        assert rep2.outer == 3 and p2 == p_whole
+        assert rep2.value == whole.value and rep2.eta_p == whole.eta_p
     ref = om.solve(inst["prob"], gaussian_factor(inst["N"], 2, 3))
-    assert rep2.status == mds.OK and rep2.eta_max <= 1e-8
-    assert abs(rep2.value - ref["value"]) <= 1e-9 * abs(ref["value"])
+    assert rep3.status == mds.OK and rep3.eta_max <= 1e-8
+    assert abs(rep3.value - ref["value"]) <= 1e-9 * abs(ref["value"])
