@@ -50,6 +50,7 @@ extern "C" {
 #define MANIDSDP_E_TIMEOUT (-4)   /* a device-side wait hit its iteration cap */
 #define MANIDSDP_E_CUDA (-5)      /* a CUDA runtime call failed */
 #define MANIDSDP_E_NOMEM (-6)     /* device allocation failed */
+#define MANIDSDP_E_TOOLARGE (-7)  /* input larger than a fixed-size scratch allows */
 
 /* ---- enums ---------------------------------------------------------------- */
 #define MANIDSDP_C_ZERO 0  /* C = 0 (BQP moment relaxations, Section 6.1) */
@@ -211,6 +212,45 @@ int manidsdp_hessvec(manidsdp_ctx* ctx, const double* Y, const double* U, int32_
  */
 int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t which, int32_t k,
                      double* lambda, double* v, int32_t* steps);
+
+/*
+ * manidsdp_lanczos_dense_noalloc - extreme eigenpair of X - Diag(d) for a dense
+ * symmetric matrix the caller already holds, without allocating device memory.
+ * The paper has no counterpart: it is the certificate check of Algorithm 1
+ * (steps 7-9, the same Lanczos iteration, stopping rules and sign convention as
+ * manidsdp_lanczos) offered without a context, for callers that must not
+ * allocate at the call site - e.g. a serving loop whose device memory is held
+ * by a caching allocator (a cudaMalloc there can fail although the cache has
+ * free blocks) or one that cannot take the device-wide synchronisation a
+ * cudaFree implies.  Its Krylov basis lives in one static device array of the
+ * library (4.4 MiB, reserved when the library's module loads on a device).
+ *   N       order of X, 1 <= N <= 16384.
+ *   X       device N x N FP64, row-major, symmetric (only read).  Must be
+ *           readable by the current device: its device memory, managed memory
+ *           or registered host memory; anything else gives E_ARG.
+ *   d       device N FP64 subtracted on the diagonal, or NULL for none; e.g.
+ *           X = Xt + D and d = z = diag((Xt + D) Y Y') give the certificate.
+ *   which   MANIDSDP_EIG_MIN or MANIDSDP_EIG_MAX.
+ *   k       Lanczos steps at most (k <= 0: min(N, 64); capped at N).
+ *           Limits: k <= 256 and k * N <= 524288; beyond them, or N > 16384,
+ *           the call returns MANIDSDP_E_TOOLARGE and does nothing else.
+ *   lambda  host: the Ritz value.  v: host or device N FP64, unit norm, first
+ *           entry above 1e-14 in magnitude positive (may be NULL).
+ *   steps   host, may be NULL.  stream: cudaStream_t as void* (NULL = legacy
+ *           default stream); it must belong to the current device.
+ * The call returns after its work on the stream has finished.  Nothing in the
+ * scratch needs to be zero beforehand: each call clears what it accumulates.
+ * Calls on the same device share the scratch: two calls in flight at the same
+ * time on one device (two streams or two host threads) corrupt each other, so
+ * serialise them.  The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture begins on the device.
+ * Errors: E_ARG (bad arguments), E_TOOLARGE (limits above), E_NONFINITE,
+ * E_CUDA (a CUDA call failed; the scratch lookup is retried on the next call).
+ */
+int manidsdp_lanczos_dense_noalloc(int32_t N, const double* X, const double* d, int32_t which,
+                                   int32_t k, double* lambda, double* v, int32_t* steps,
+                                   void* stream);
 
 /*
  * manidsdp_solve - Algorithm 1 from the starting matrix Y0 (host or device,

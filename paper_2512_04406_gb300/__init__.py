@@ -28,6 +28,7 @@ __all__ = [
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+E_TOOLARGE = -7
 C_ZERO, C_DENSE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 EIG_MIN, EIG_MAX = 0, 1
@@ -105,6 +106,10 @@ _sig = {
     "manidsdp_ucqp_index_map": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int64), _P]),
     "manidsdp_ucqp_rhs": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P]),
+    "manidsdp_lanczos_dense_noalloc": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                                      ctypes.c_int32,
+                                                      ctypes.POINTER(ctypes.c_double), _P,
+                                                      ctypes.POINTER(ctypes.c_int32), _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -220,6 +225,21 @@ def manidsdp_lanczos(ctx: Context, Y, p: int, which: int = EIG_MIN, k: int = 0, 
     st = _lib.manidsdp_lanczos(ctx, _ptr(Y, np.float64), p, which, k, ctypes.byref(lam),
                                _ptr(v, np.float64, True), ctypes.byref(steps))
     _check(st, "manidsdp_lanczos")
+    return lam.value, steps.value
+
+
+def manidsdp_lanczos_dense_noalloc(X, d=None, which: int = EIG_MIN, k: int = 0, v=None,
+                                   stream: int | None = None):
+    """Extreme eigenpair of X - Diag(d) for a device N x N FP64 matrix X (and an
+    optional device N-vector d), computed in the library's static scratch with no
+    device allocation.  Returns (lambda, steps); v (N FP64) receives the vector."""
+    N = int(X.shape[0])
+    lam = ctypes.c_double()
+    steps = ctypes.c_int32()
+    st = _lib.manidsdp_lanczos_dense_noalloc(N, _ptr(X, np.float64), _ptr(d, np.float64), which, k,
+                                            ctypes.byref(lam), _ptr(v, np.float64, True),
+                                            ctypes.byref(steps), stream)
+    _check(st, "manidsdp_lanczos_dense_noalloc")
     return lam.value, steps.value
 
 

@@ -611,6 +611,7 @@ const char* manidsdp_strerror(int status) {
     case MANIDSDP_E_TIMEOUT: return "device-side wait timed out";
     case MANIDSDP_E_CUDA: return "CUDA runtime error";
     case MANIDSDP_E_NOMEM: return "device allocation failed";
+    case MANIDSDP_E_TOOLARGE: return "input exceeds the fixed-size scratch of a no-alloc entry point";
     default: return "unknown status";
   }
 }
