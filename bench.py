@@ -53,7 +53,12 @@ UNIT = "s/ALM-outer-iteration"
 # steps of a GPU run), used to scale the sampled oracle timings to one outer
 # iteration when no GPU run precedes them.  The GPU arm uses the counts of its
 # own timed steps.
-DEFAULT_COUNTS = dict(hessvecs=400, evals=40, grads=30, lanczos_matvecs=300, p=100)
+DEFAULT_COUNTS = dict(hessvecs=7035, evals=166, grads=170, lanczos_matvecs=122, p=51)
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one
+# Hess-vec) from one ncu capture at q = 80 and the p of the timed steps, per gather-GEMM
+# engine of the mixed form; None when no capture matches the current kernels.
+HV_TRAFFIC = {"fma": {"p": 51, "bytes": 191.1e6}, "tc": {"p": 51, "bytes": 183.4e6}}
 
 
 def parse():
@@ -65,6 +70,9 @@ def parse():
     ap.add_argument("--q", type=int, default=80)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--engine", choices=["fma", "tc"], default="fma",
+                    help="gather GEMM of the FP32 Hessian-vector product: FP32 FMA kernel or "
+                         "tensor cores (tcgen05 kind::tf32, 3xTF32 split)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -282,6 +290,7 @@ def main():
     prm.precision_mode = prec
     prm.p_max = 256
     prm.profile = 1
+    prm.tensor_cores = 1 if args.engine == "tc" else 0
     if args.tcg_host:
         prm.tcg_device = 0
     stream = torch.cuda.current_stream()
@@ -292,6 +301,7 @@ def main():
         fp_bytes = 4 if prec == mds.PREC_MIXED else 8
         byt = hessvec_bytes(N, m, N * (N + 1) // 2, m, p, fp_bytes)
         print(json.dumps({"hv_only": True, "q": args.q, "N": N, "p": p, "precision": args.precision,
+                          "engine": args.engine,
                           "ms": ms, "gbs": byt / (ms * 1e-3) / 1e9,
                           "tflops": 6.0 * N * N * p / (ms * 1e-3) / 1e12}), flush=True)
         mds.manidsdp_destroy(ctx)
@@ -347,8 +357,10 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     if prec == mds.PREC_MIXED:
+        tr = HV_TRAFFIC.get(args.engine)
         roof = {"bound": "hbm", "achieved": bytes_live / (hv_ms_live * 1e-3) / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "traffic": None, "peak_source": peak_src,
+                "unit": "GB/s", "traffic": tr["bytes"] if tr else None,
+                "traffic_at_p": tr["p"] if tr else None, "peak_source": peak_src,
                 "kernel": "Hessian-vector product (FP32 class means + gather GEMM + epilogue)",
                 "avg_ms": hv_ms_live, "p_avg": p_avg,
                 "isolated_ms_at_p0": hv_ms_iso,
@@ -367,6 +379,7 @@ def main():
         # solve of W + K outer iterations from a host start, host outputs
         pe = mds.manidsdp_default_params()
         pe.precision_mode = prec
+        pe.tensor_cores = prm.tensor_cores
         pe.max_outer = args.warmup + args.steps
         y_host = np.empty(m)
         torch.cuda.synchronize()
@@ -389,6 +402,7 @@ def main():
         Qs, cs, Ns, ms_, idxs, bs, p0s = workload(args.solve_q, args.seed)
         ps = mds.manidsdp_default_params()
         ps.precision_mode = prec
+        ps.tensor_cores = prm.tensor_cores
         cs_ = mds.manidsdp_setup(Ns, ms_, idxs, bs, params=ps, stream=stream.cuda_stream)
         Y0s = torch.tensor(gaussian_factor(Ns, p0s, args.seed), device="cuda")
         torch.cuda.synchronize()
@@ -409,6 +423,7 @@ def main():
         for name, pm in (("mixed", mds.PREC_MIXED), ("fp64", mds.PREC_FP64)):
             pc = mds.manidsdp_default_params()
             pc.precision_mode = pm
+            pc.tensor_cores = prm.tensor_cores
             cx = mds.manidsdp_setup(Nc, mc, idxc, bc, params=pc, stream=stream.cuda_stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -438,6 +453,8 @@ def main():
             "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
             "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
                        "N": N, "m": m, "p0": p0, "precision": args.precision,
+                       "hessvec_gemm": "tensor cores (tcgen05 kind::tf32, 3xTF32)" if args.engine == "tc"
+                       else "FP32 FMA",
                        "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
                        "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",
                        "parallelism": f"replicas{world}"},

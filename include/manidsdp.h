@@ -97,6 +97,11 @@ typedef struct {
                              negative-curvature direction left by the previous solve
                              (Y0/p0 ignored; a fresh start when no solve ran yet);
                              0 (default): start from Y0 with Xt = 0, sigma0 */
+  int32_t tensor_cores;   /* mixed form only: 1 runs the gather GEMM of the FP32
+                             Hessian-vector product on the tensor cores
+                             (tcgen05 kind::tf32, each operand split into two TF32
+                             halves, three products per step, FP32 accumulation);
+                             0 (default): FP32 FMA kernel */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */

@@ -214,6 +214,7 @@ struct manidsdp_ctx {
   int resume_p = 0;
   double resume_rscale = -1.0;
   int resume_outer = 0;
+  int* tc_err = nullptr;  // set by a tensor-core kernel whose device-side wait timed out
   bool resume_have_U = false;  // the last iteration augmented Y = [Y, 0] and set U = [0, V]
   int resume_U_cols = 0;
   // counters and phase timers
@@ -281,6 +282,30 @@ void dots(manidsdp_ctx* c, size_t n, int k, const double* x0, const double* y0, 
 bool mixed(const manidsdp_ctx* c) { return c->prm.precision_mode == MANIDSDP_PREC_MIXED; }
 // The FP32 copy of G read by the mixed-precision Hess-vec.
 float* g32(manidsdp_ctx* c) { return mixed(c) ? c->Gh : c->Gf; }
+
+// T = G U - sigma A*(w) Y of the FP32 Hessian-vector product as split-K partial
+// products in c->gws (tensor cores or FP32 FMA); returns the number of splits.
+int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
+  if (c->prm.tensor_cores)
+    return launch_tc_gather_gemm_partials(c->N, p, g32(c), c->Upf, c->idx, c->wf,
+                                          float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
+                                          c->tc_err, s);
+  return launch_gemm32_partials(c->N, p, g32(c), c->Upf, c->idx, c->wf, float(-c->sigma), c->Yf,
+                                c->gws, c->gws_bytes, s);
+}
+
+void drop_graphs(manidsdp_ctx* c);
+
+// MANIDSDP_E_TIMEOUT when a tensor-core kernel reported an expired wait (the
+// flag is cleared); synchronises the context's stream.
+int take_device_error(manidsdp_ctx* c) {
+  int e = 0;
+  MDS_CUDA(cudaMemcpyAsync(&e, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  MDS_CUDA(cudaStreamSynchronize(c->s));
+  if (e == 0) return MANIDSDP_OK;
+  MDS_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->s));
+  return MANIDSDP_E_TIMEOUT;
+}
 
 // Psi, y and G at Y.  FP64 mode: native FP64, G (and Gf = float(G) when given).
 // Mixed mode: df64 on the FP32 pipe, G as the float pair (Gh, Gl) and, when
@@ -363,8 +388,7 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
     mark(2);
-    const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
-                                              float(-c->sigma), c->Yf, c->gws, c->gws_bytes, c->s);
+    const int splits = gather_gemm32(c, p, c->s);
     mark(3);
     launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
     launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
@@ -528,6 +552,7 @@ void default_params(manidsdp_params* p) {
   p->verbose = 0;
   p->profile = 0;
   p->tcg_device = 1;
+  p->tensor_cores = 0;
 }
 
 struct NonFinite {};
@@ -691,6 +716,9 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     MDS_CUDA(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
     c->idx = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+    c->tc_err = dalloc<int>(c, 1);
+    MDS_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->s));
+    tc_gather_gemm_prepare();
     c->mult = dalloc<double>(c, m);
     MDS_CUDA(cudaMemcpyAsync(c->mult, mult.data(), m * sizeof(double), cudaMemcpyHostToDevice, c->s));
     c->b = dalloc<double>(c, m);
@@ -810,8 +838,10 @@ int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
       prm->p0 > prm->p_max || prm->p_min < 1 || prm->delta_max < 0 || prm->lanczos_k < 1 ||
       prm->precision_mode != c->prm.precision_mode)
     return MANIDSDP_E_ARG;
+  const bool engine_changed = prm->tensor_cores != c->prm.tensor_cores;
   c->prm = *prm;
   c->kmax = std::min(std::max(c->prm.lanczos_k, 1), std::min(c->kmax, c->N));
+  if (engine_changed) drop_graphs(c);  // cached tCG graphs hold the old gather GEMM
   return MANIDSDP_OK;
 }
 
@@ -891,7 +921,7 @@ int manidsdp_hessvec(manidsdp_ctx* c, const double* Y, const double* U, int32_t 
     hessvec(c, c->Y, c->delta, p, c->Hd, precision);
     MDS_CUDA(cudaMemcpyAsync(HU, c->Hd, np * sizeof(double), cudaMemcpyDefault, c->s));
     sync(c);
-    return MANIDSDP_OK;
+    return take_device_error(c);
   });
 }
 
@@ -1026,8 +1056,7 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
     launch_tcg_prep<float>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, c->Upf, s);
     float* pbf = reinterpret_cast<float*>(c->piece_buf);
     launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
-    const int splits = launch_gemm32_partials(N, p, g32(c), c->Upf, c->idx, c->wf,
-                                              float(-c->sigma), c->Yf, c->gws, c->gws_bytes, s);
+    const int splits = gather_gemm32(c, p, s);
     launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
     launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
                 static_cast<float*>(c->gws) + size_t(splits) * N * p, s);
@@ -1382,7 +1411,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     }
     sync(c);
     c->eval_ok = false;
-    return MANIDSDP_OK;
+    return take_device_error(c);
   });
   if (report) *report = rep;
   if (gst != MANIDSDP_OK) return gst;
