@@ -59,58 +59,58 @@ def index_map_enumerated(q: int, order: int = 2):
     return idx
 
 
-def _comb_rank(sets: np.ndarray, q: int) -> np.ndarray:
-    """Lexicographic rank of each sorted d-subset (rows of ``sets``) among all
-    d-subsets of {0..q-1}: the number of d-subsets that precede it.  A subset
-    (c_1 < ... < c_d) is preceded by every subset sharing its first i-1
-    elements and having a smaller i-th element j (c_{i-1} < j < c_i); there are
-    C(q-1-j, d-i) of those for each such j."""
-    n, d = sets.shape
-    r = np.zeros(n, dtype=np.int64)
-    prev = np.full(n, -1, dtype=np.int64)
-    table = np.array([[comb(a, b) for b in range(d + 1)] for a in range(q + 1)], dtype=np.int64)
-    for i in range(d):
-        ci = sets[:, i].astype(np.int64)
-        for j in range(q):
-            mask = (j > prev) & (j < ci)
-            if mask.any():
-                r[mask] += table[q - 1 - j, d - i - 1]
+def _lex_rank(sets: np.ndarray, q: int, d: int, table: np.ndarray) -> np.ndarray:
+    """Lexicographic rank of each sorted d-subset (the first d columns of
+    ``sets``) among all d-subsets of {0..q-1}: the number of d-subsets that
+    precede it.  A subset (c_1 < ... < c_d) is preceded by every subset that
+    shares its first i-1 elements and has a smaller i-th element j
+    (c_{i-1} < j < c_i), C(q-1-j, d-i) of them for each such j; summed over j
+    (hockey-stick identity) that is C(q-1-c_{i-1}, d-i+1) - C(q-c_i, d-i+1),
+    with c_0 = -1.  ``table[n, k]`` = C(n, k)."""
+    r = np.zeros(sets.shape[0], dtype=np.int64)
+    prev = np.full(sets.shape[0], -1, dtype=np.int64)
+    for i in range(1, d + 1):
+        ci = sets[:, i - 1]
+        r += table[q - 1 - prev, d - i + 1] - table[q - ci, d - i + 1]
         prev = ci
     return r
 
 
-def index_map(q: int, order: int = 2) -> np.ndarray:
-    """Vectorised idx map, identical to ``index_map_enumerated``.  Each basis
-    monomial is a bit set; the product monomial is the xor of two bit sets; its
-    rank is the degree offset plus the lexicographic rank of its sorted index
-    tuple."""
+def index_map(q: int, order: int = 2, block: int = 256) -> np.ndarray:
+    """Vectorised idx map, identical to ``index_map_enumerated``.  For a block
+    of rows at a time: the variables of the two basis monomials of each entry
+    (padded with q), sorted; a variable present twice cancels (x_i^2 = 1), which
+    leaves the sorted symmetric difference; its rank is the degree offset plus
+    its lexicographic rank among the monomials of that degree."""
     B = basis(q, order)
     N = len(B)
-    # basis monomials padded to two slots with -1 for missing variables
-    el = np.full((N, 2), -1, dtype=np.int64)
+    el = np.full((N, order), q, dtype=np.int64)
     for a, beta in enumerate(B):
-        for s, v in enumerate(beta):
-            el[a, s] = v
-    # symmetric difference via a q-wide indicator (q <= 200 in practice)
-    ind = np.zeros((N, q), dtype=np.int8)
-    for s in range(2):
-        ok = el[:, s] >= 0
-        ind[np.nonzero(ok)[0], el[ok, s]] = 1
+        for s_, v in enumerate(beta):
+            el[a, s_] = v
     offsets = np.cumsum([0] + [comb(q, d) for d in range(0, 2 * order + 1)])
-    idx = np.empty((N, N), dtype=np.int64)
-    for a in range(N):
-        x = ind[a][None, :] ^ ind  # (N, q)
-        deg = x.sum(axis=1)
-        out = np.empty(N, dtype=np.int64)
-        for d in np.unique(deg):
-            rows = np.nonzero(deg == d)[0]
-            if d == 0:
-                out[rows] = 0
-                continue
-            sets = np.nonzero(x[rows])[1].reshape(len(rows), d)
-            out[rows] = offsets[d] + _comb_rank(sets, q)
-        idx[a] = out
-    return idx.astype(np.int32)
+    table = np.array([[comb(n, k) for k in range(2 * order + 2)] for n in range(q + 2)],
+                     dtype=np.int64)
+    idx = np.empty((N, N), dtype=np.int32)
+    for r0 in range(0, N, block):
+        rows = el[r0:r0 + block]
+        nb = rows.shape[0]
+        v = np.concatenate([np.broadcast_to(rows[:, None, :], (nb, N, order)),
+                            np.broadcast_to(el[None, :, :], (nb, N, order))], axis=2)
+        v = np.sort(v, axis=2)
+        same = (v[..., 1:] == v[..., :-1]) & (v[..., 1:] < q)
+        gone = np.zeros(v.shape, dtype=bool)
+        gone[..., 1:] |= same
+        gone[..., :-1] |= same
+        v = np.sort(np.where(gone, q, v), axis=2).reshape(nb * N, 2 * order)
+        deg = (v < q).sum(axis=1)
+        out = np.zeros(nb * N, dtype=np.int64)
+        for d in range(1, 2 * order + 1):
+            sel = np.nonzero(deg == d)[0]
+            if len(sel):
+                out[sel] = offsets[d] + _lex_rank(v[sel], q, d, table)
+        idx[r0:r0 + nb] = out.reshape(nb, N)
+    return idx
 
 
 def multiplicities(idx: np.ndarray, m: int) -> np.ndarray:

@@ -13,8 +13,8 @@ def torch_cuda():
     return torch
 
 
-def instance(q, seed=0, order=2):
-    Q, c = bqp_instance(q, seed)
+def instance(q, seed=0, order=2, density=None):
+    Q, c = bqp_instance(q, seed, density)
     N, m, idx = mds.manidsdp_bqp_index_map(q, order)
     b = mds.manidsdp_bqp_rhs(q, Q, c, order)
     ref_idx = moment.index_map(q, order)
