@@ -57,8 +57,14 @@ DEFAULT_COUNTS = dict(hessvecs=7035, evals=166, grads=170, lanczos_matvecs=122, 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one
 # Hess-vec) from one ncu capture at q = 80 and the p of the timed steps, per gather-GEMM
-# engine of the mixed form; None when no capture matches the current kernels.
-HV_TRAFFIC = {"fma": {"p": 51, "bytes": 191.1e6}, "tc": {"p": 51, "bytes": 183.4e6}}
+# engine of the mixed form.  "current" is False when kernels of the Hess-vec changed
+# after the capture; the line then reports traffic null and the capture as context.
+HV_TRAFFIC = {
+    "fma": {"p": 51, "bytes": 191.1e6, "current": False,
+            "note": "captured before the FP32 Gram moved to 32-row splits on a side stream"},
+    "tc": {"p": 51, "bytes": 183.4e6, "current": False,
+           "note": "captured before the tensor-core kernel drained its accumulator in chains"},
+}
 
 
 def parse():
@@ -72,7 +78,7 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--engine", choices=["fma", "tc"], default="fma",
                     help="gather GEMM of the FP32 Hessian-vector product: FP32 FMA kernel or "
-                         "tensor cores (tcgen05 kind::tf32, 3xTF32 split)")
+                         "tensor cores (tcgen05 kind::tf32, two-term TF32 operand split)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -359,8 +365,8 @@ def main():
     if prec == mds.PREC_MIXED:
         tr = HV_TRAFFIC.get(args.engine)
         roof = {"bound": "hbm", "achieved": bytes_live / (hv_ms_live * 1e-3) / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "traffic": tr["bytes"] if tr else None,
-                "traffic_at_p": tr["p"] if tr else None, "peak_source": peak_src,
+                "unit": "GB/s", "traffic": tr["bytes"] if tr and tr["current"] else None,
+                "traffic_last_capture": tr, "peak_source": peak_src,
                 "kernel": "Hessian-vector product (FP32 class means + gather GEMM + epilogue)",
                 "avg_ms": hv_ms_live, "p_avg": p_avg,
                 "isolated_ms_at_p0": hv_ms_iso,
@@ -453,7 +459,7 @@ def main():
             "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
             "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
                        "N": N, "m": m, "p0": p0, "precision": args.precision,
-                       "hessvec_gemm": "tensor cores (tcgen05 kind::tf32, 3xTF32)" if args.engine == "tc"
+                       "hessvec_gemm": "tensor cores (tcgen05 kind::tf32, operands split into two TF32 halves)" if args.engine == "tc"
                        else "FP32 FMA",
                        "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
                        "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",

@@ -229,6 +229,10 @@ struct manidsdp_ctx {
   void* tcgst = nullptr;
   double *kpart = nullptr, *rpart = nullptr;
   cudaStream_t cs = nullptr;
+  // side stream of the FP32 Hess-vec: U'Y and the Y(U'Y) + U(Y'Y) slice run on it
+  // while the class sums and the gather GEMM run on the main (or capture) stream
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct Graph {
     int p, prec;
     double sigma;
@@ -295,6 +299,38 @@ int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
 }
 
 void drop_graphs(manidsdp_ctx* c);
+
+int gather_gemm32_splits(manidsdp_ctx* c, int p) {
+  return c->prm.tensor_cores ? tc_gather_gemm_splits(c->N, p, c->gws_bytes)
+                             : gemm32_splits(c->N, p, c->gws_bytes);
+}
+
+// The FP32 Hess-vec after its prologue (Upf, Yf, Y'Y in place) up to the
+// split-K partials in c->gws: class sums and gather GEMM on s; U'Y and the
+// Y(U'Y) + U(Y'Y) slice on the side stream when fork is set (joined before
+// return), else on s after the GEMM.  Returns the number of GEMM splits.
+int hessvec32_body(manidsdp_ctx* c, int p, cudaStream_t s, bool fork) {
+  const int N = c->N;
+  const int splits = gather_gemm32_splits(c, p);
+  float* ym_out = static_cast<float*>(c->gws) + size_t(splits) * N * p;
+  if (fork) {
+    MDS_CUDA(cudaEventRecord(c->ev_fork, s));
+    MDS_CUDA(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s2);
+    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma), ym_out, c->s2);
+    MDS_CUDA(cudaEventRecord(c->ev_join, c->s2));
+  }
+  float* pbf = reinterpret_cast<float*>(c->piece_buf);
+  launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
+  if (gather_gemm32(c, p, s) != splits) throw DeviceError{cudaErrorInvalidValue};
+  if (fork) {
+    MDS_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+  } else {
+    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
+    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma), ym_out, s);
+  }
+  return splits;
+}
 
 // MANIDSDP_E_TIMEOUT when a tensor-core kernel reported an expired wait (the
 // flag is cleared); synchronises the context's stream.
@@ -385,15 +421,20 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
       launch_gram2<float>(N, p, c->Yf, nullptr, c->Yf, c->M1f + size_t(p) * p, c->gws2,
                           c->gws2_bytes, c->s);
     mark(1);
-    float* pbf = reinterpret_cast<float*>(c->piece_buf);
-    launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
-    mark(2);
-    const int splits = gather_gemm32(c, p, c->s);
-    mark(3);
-    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
-    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
-                static_cast<float*>(c->gws) + size_t(splits) * N * p, c->s);
-    mark(4);
+    int splits;
+    if (stages) {  // serial, with the stage events between the steps
+      float* pbf = reinterpret_cast<float*>(c->piece_buf);
+      launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
+      mark(2);
+      splits = gather_gemm32(c, p, c->s);
+      mark(3);
+      launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, c->s);
+      launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
+                  static_cast<float*>(c->gws) + size_t(splits) * N * p, c->s);
+      mark(4);
+    } else {
+      splits = hessvec32_body(c, p, c->s, true);
+    }
     launch_hv_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), nullptr, Y, c->Up,
                               c->z, c->sigma, HU, c->s);
   }
@@ -589,6 +630,9 @@ void release(manidsdp_ctx* c) {
   }
   c->graphs.clear();
   if (c->cs) cudaStreamDestroy(c->cs);
+  if (c->s2) cudaStreamDestroy(c->s2);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   c->cs = nullptr;
 }
 
@@ -714,6 +758,9 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     MDS_CUDA(cudaEventCreate(&c->ev1));
     for (auto& e : c->sev) MDS_CUDA(cudaEventCreate(&e));
     MDS_CUDA(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    MDS_CUDA(cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking));
+    MDS_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    MDS_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     c->idx = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
     c->tc_err = dalloc<int>(c, 1);
@@ -1054,12 +1101,7 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
                                 c->Up, c->z, c->sigma, c->delta, c->Hd, c->kpart, s);
   } else {
     launch_tcg_prep<float>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, c->Upf, s);
-    float* pbf = reinterpret_cast<float*>(c->piece_buf);
-    launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
-    const int splits = gather_gemm32(c, p, s);
-    launch_gram2<float>(N, p, c->Upf, nullptr, c->Yf, c->M1f, c->gws2, c->gws2_bytes, s);
-    launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma),
-                static_cast<float*>(c->gws) + size_t(splits) * N * p, s);
+    const int splits = hessvec32_body(c, p, s, true);
     launch_tcg_epilogue<float>(N, p, splits, static_cast<const float*>(c->gws), nullptr, c->Y,
                                c->Up, c->z, c->sigma, c->delta, c->Hd, c->kpart, s);
   }

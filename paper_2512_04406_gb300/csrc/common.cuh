@@ -126,11 +126,15 @@ int launch_gemm32_partials(int N, int ncol, const float* G, const float* U, cons
 void launch_ym32(int N, int p, const float* Y, const float* Up, const float* M, float scale,
                  float* out, cudaStream_t s);
 
-// The same partial products on the tensor cores (tcgen05 kind::tf32, 3xTF32
+// The same partial products on the tensor cores (tcgen05 kind::tf32, two-term TF32
 // split), kernels_tc.cu.  ncol <= 256.  *err is set to 1 when a device-side wait
 // of a CTA hit its limit.  tc_gather_gemm_prepare raises the kernel's dynamic
 // shared-memory limit; call it once per device before the first launch.
 void tc_gather_gemm_prepare();
+// Number of split-K partial products the launchers below (and launch_gemm32_partials)
+// will write for these sizes; the YM slice goes right after them.
+int tc_gather_gemm_splits(int N, int ncol, size_t ws_bytes);
+int gemm32_splits(int N, int ncol, size_t ws_bytes);
 int launch_tc_gather_gemm_partials(int N, int ncol, const float* G, const float* U,
                                    const int32_t* idx, const float* w, float gscale,
                                    const float* Y, void* ws, size_t ws_bytes, int* err,

@@ -314,7 +314,8 @@ void launch_gram2(int N, int p, const T* A1, const T* A2, const T* B, T* out, vo
   const int nmat = A2 != nullptr ? 2 : 1;
   const int gx = (p + 63) / 64, gy = (p + 63) / 64;
   int splits = (2 * 152 + nmat * gx * gy - 1) / (nmat * gx * gy);
-  splits = std::min(splits, (N + 63) / 64);
+  // FP32 (the tCG Hess-vec, where this Gram is on the critical path): splits of 32 rows
+  splits = std::min(splits, sizeof(T) == 4 ? (N + 31) / 32 : (N + 63) / 64);
   const size_t per = size_t(nmat) * p * p * sizeof(T);
   if (size_t(splits) * per > ws_bytes) splits = int(ws_bytes / per);
   if (splits < 1) splits = 1;

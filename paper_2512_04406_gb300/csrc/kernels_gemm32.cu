@@ -188,10 +188,8 @@ void launch_ym32(int N, int p, const float* Y, const float* Up, const float* M, 
   MDS_CUDA(cudaGetLastError());
 }
 
-template <int BN, int TN>
-static int gemm32_cfg(int N, int ncol, const float* G, const float* U, const int32_t* idx,
-                      const float* w, float gscale, const float* Y, void* ws, size_t ws_bytes,
-                      cudaStream_t s) {
+template <int BN>
+static int gemm32_split_count(int N, int ncol, size_t ws_bytes, int* kchunk_out) {
   const int gx = (ncol + BN - 1) / BN, gy = (N + 127) / 128;
   // about four blocks per SM (the kernel holds up to three per SM), each split >= 64 K-rows
   int splits = (4 * 152 + gx * gy - 1) / (gx * gy);
@@ -201,13 +199,29 @@ static int gemm32_cfg(int N, int ncol, const float* G, const float* U, const int
   if (splits < 1) throw DeviceError{cudaErrorMemoryAllocation};
   int kchunk = (N + splits - 1) / splits;
   kchunk = (kchunk + 7) / 8 * 8;
-  splits = (N + kchunk - 1) / kchunk;
-  dim3 grid(gx, gy, splits);
+  if (kchunk_out) *kchunk_out = kchunk;
+  return (N + kchunk - 1) / kchunk;
+}
+
+template <int BN, int TN>
+static int gemm32_cfg(int N, int ncol, const float* G, const float* U, const int32_t* idx,
+                      const float* w, float gscale, const float* Y, void* ws, size_t ws_bytes,
+                      cudaStream_t s) {
+  int kchunk = 0;
+  const int splits = gemm32_split_count<BN>(N, ncol, ws_bytes, &kchunk);
+  dim3 grid((ncol + BN - 1) / BN, (N + 127) / 128, splits);
   count_launches(1);
   gemm32_kernel<BN, TN><<<grid, 256, 0, s>>>(N, ncol, kchunk, G, U, idx, w, gscale, Y,
                                              static_cast<float*>(ws));
   MDS_CUDA(cudaGetLastError());
   return splits;
+}
+
+int gemm32_splits(int N, int ncol, size_t ws_bytes) {
+  if (ncol <= 16) return gemm32_split_count<16>(N, ncol, ws_bytes, nullptr);
+  if (ncol <= 32) return gemm32_split_count<32>(N, ncol, ws_bytes, nullptr);
+  if (ncol <= 64) return gemm32_split_count<64>(N, ncol, ws_bytes, nullptr);
+  return gemm32_split_count<128>(N, ncol, ws_bytes, nullptr);
 }
 
 int launch_gemm32_partials(int N, int ncol, const float* G, const float* U, const int32_t* idx,

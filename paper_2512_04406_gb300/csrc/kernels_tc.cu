@@ -8,16 +8,17 @@
 // (split K; each split writes its partial product, reduced by the Hessian
 // epilogue).  Per chunk of 16 values of g, 256 threads load 128 x 16 entries of
 // G and of the index map (gathering w), 16 rows of U and of Y, split every
-// value x into x = hi + lo (hi: x rounded to TF32, lo = x - hi) and store both
+// value x into x ~ hi + lo (hi = tf32(x), lo = tf32(x - hi)) and store both
 // halves in shared memory in the
 // K-major core-matrix layout of tcgen05 (8 rows x 16 bytes per core matrix).
-// One thread then issues tcgen05.mma kind::tf32 for the three products
-// hi*hi + hi*lo + lo*hi per K step of 8 (the "3xTF32" split: about 2^-21
+// One thread then issues tcgen05.mma kind::tf32 for the four products
+// lo*lo + lo*hi + hi*lo + hi*hi per K step of 8 (smallest first; about 2^-22
 // relative error per product, FP32 accumulation in tensor memory) and commits
 // them to an mbarrier; two shared-memory stages let the next chunk's loads and
-// stores overlap the running MMAs.  The accumulator (128 lanes x p columns of
-// FP32 in TMEM) is read back with tcgen05.ld by the four warps whose lane
-// quarters cover the 128 rows.
+// stores overlap the running MMAs.  Every 8 chunks, and at the end, the
+// accumulator (128 lanes x p columns of FP32 in TMEM) is read back with
+// tcgen05.ld by the four warps whose lane quarters cover the 128 rows and added
+// into the CTA's partial product in global memory.
 //
 // Every wait on an mbarrier is bounded (about two seconds of SM clock); on
 // expiry the CTA records an error in *err, waits (bounded) for its MMAs in
@@ -34,6 +35,12 @@ constexpr int kTcG = 16;            // values of g per chunk
 constexpr int kTcThreads = 256;
 constexpr int kTcATile = kTcBM * 2 * kTcG * 4;  // bytes of one 128 x 32 FP32 operand tile
 constexpr long long kTcSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
+// Chunks accumulated in tensor memory before the accumulator is added into the
+// partial product in global memory (FP32, round to nearest): 8 chunks = 256 K
+// values per accumulation chain.  The tensor core's own FP32 accumulation loses
+// accuracy in proportion to the chain length (measured: 1.3e-5 relative Hess-vec
+// error with 590-term chains at N = 3241, 9.5e-5 with 2906-term chains at N = 7261).
+constexpr int kTcDrain = 8;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -108,12 +115,18 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-// x = hi + lo with hi = x rounded to the nearest TF32 value (ties away from zero:
-// add half a TF32 unit to the magnitude bits, clear the 13 low bits) and lo = x - hi,
-// exact in FP32 (Sterbenz); |lo| <= 2^-11 |hi|.
+// Round to the nearest TF32 value (ties away from zero): add half a TF32 unit to
+// the magnitude bits and clear the 13 low bits.
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+// x ~ hi + lo, both exact TF32 values: hi = tf32(x), lo = tf32(x - hi) (x - hi is
+// exact in FP32 by Sterbenz, |x - hi| <= 2^-11 |x|), so |x - hi - lo| <= 2^-23 |x|,
+// the representation error of FP32 itself; rounding lo in software keeps the
+// tensor core from truncating it (a bias that grows with the length of the sum).
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-  lo = x - hi;
+  hi = round_tf32(x);
+  lo = round_tf32(x - hi);
 }
 
 // 16 FP32 columns of this warp's 32 TMEM lanes: thread i gets lane (base lane + i).
@@ -261,6 +274,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t idesc = tc_idesc(np);
   bool failed = false;
   int last = -1;  // last chunk whose MMAs were committed
+  bool drained = false;  // the partial product already holds earlier chains
+  float* op = part + size_t(blockIdx.y) * N * ncol;
+  // warps 0-3 (lane quarters 0-3 of TMEM): row m0 + warp * 32 + lane of the
+  // accumulator into the partial product, written (add = false) or added
+  auto drain = [&](bool add) {
+    if (warp < 4) {
+      const int row = m0 + warp * 32 + lane;
+      for (int c0 = 0; c0 < np; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
+        if (row < N) {
+          float* dst = op + size_t(row) * ncol + c0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < ncol) dst[i] = add ? dst[i] + v[i] : v[i];
+        }
+      }
+    }
+  };
   if (nchunks > 0) {
     load_idx(0);
     load_rest(0);
@@ -292,13 +324,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t ko = kk * 256;  // two core matrices of K per step of 8
         const uint64_t dah = tc_desc(ahi + ko, 128, 1024), dal = tc_desc(alo + ko, 128, 1024);
         const uint64_t dbh = tc_desc(bhi + ko, 128, 1024), dbl = tc_desc(blo + ko, 128, 1024);
-        tc_mma(tmem, dal, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+        tc_mma(tmem, dal, dbl, idesc, (c % kTcDrain != 0 || kk > 0) ? 1u : 0u);
+        tc_mma(tmem, dal, dbh, idesc, 1u);
         tc_mma(tmem, dah, dbl, idesc, 1u);
         tc_mma(tmem, dah, dbh, idesc, 1u);
       }
       tc_commit(&bars[s]);
     }
     last = c;
+    if ((c + 1) % kTcDrain == 0 && c + 1 < nchunks) {
+      // end of an accumulation chain: wait for its MMAs, add the accumulator into
+      // the partial product; the next chunk starts a new chain
+      const bool ok = mbar_wait(&bars[s], uint32_t((c >> 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      drain(drained);
+      drained = true;
+      tc_fence_before();
+      __syncthreads();
+    }
   }
   // wait for the last committed chunk's MMAs (its commit covers all earlier
   // ones); after a failed wait this is the bounded wait for MMAs in flight
@@ -308,26 +355,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-  } else {
+  } else if (nchunks > 0) {
     tc_fence_after();
-    float* op = part + size_t(blockIdx.y) * N * ncol;
-    if (warp < 4) {
-      const int row = m0 + warp * 32 + lane;
-      for (int c0 = 0; c0 < np; c0 += 16) {
-        float v[16];
-        if (nchunks > 0) {
-          tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = 0.f;
-        }
-        if (row < N) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncol) op[size_t(row) * ncol + c0 + i] = v[i];
-        }
-      }
-    }
+    drain(drained);
+  } else if (warp < 4) {  // empty K range: a zero partial product
+    const int row = m0 + warp * 32 + lane;
+    if (row < N)
+      for (int c0 = 0; c0 < ncol; ++c0) op[size_t(row) * ncol + c0] = 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -349,16 +383,12 @@ void tc_gather_gemm_prepare() {
                                 int(tc_smem_bytes(256))));
 }
 
-int launch_tc_gather_gemm_partials(int N, int ncol, const float* G, const float* U,
-                                   const int32_t* idx, const float* w, float gscale,
-                                   const float* Y, void* ws, size_t ws_bytes, int* err,
-                                   cudaStream_t s) {
-  if (ncol < 1 || ncol > 256) throw DeviceError{cudaErrorInvalidValue};
+// Split-K layout of the kernel: one wave of CTAs (two per SM when the shared
+// memory allows), each split at least 64 values of g, K ranges in whole chunks.
+static int tc_split_count(int N, int ncol, size_t ws_bytes, int* kchunk_out) {
   const int np = (ncol + 15) / 16 * 16;
-  const size_t smem = tc_smem_bytes(np);
-  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const int per_sm = tc_smem_bytes(np) <= 110 * 1024 ? 2 : 1;
   const int gy = (N + kTcBM - 1) / kTcBM;
-  // one wave: splits x row blocks <= resident CTAs, each split >= 64 values of g
   int splits = std::max(1, (152 * per_sm) / gy);
   splits = std::min(splits, std::max(1, N / 64));
   const size_t per = size_t(N) * ncol * sizeof(float);
@@ -366,11 +396,26 @@ int launch_tc_gather_gemm_partials(int N, int ncol, const float* G, const float*
   if (splits < 1) throw DeviceError{cudaErrorMemoryAllocation};
   int kchunk = (N + splits - 1) / splits;
   kchunk = (kchunk + kTcG - 1) / kTcG * kTcG;
-  splits = (N + kchunk - 1) / kchunk;
-  dim3 grid(gy, splits);
+  if (kchunk_out) *kchunk_out = kchunk;
+  return (N + kchunk - 1) / kchunk;
+}
+
+int tc_gather_gemm_splits(int N, int ncol, size_t ws_bytes) {
+  return tc_split_count(N, ncol, ws_bytes, nullptr);
+}
+
+int launch_tc_gather_gemm_partials(int N, int ncol, const float* G, const float* U,
+                                   const int32_t* idx, const float* w, float gscale,
+                                   const float* Y, void* ws, size_t ws_bytes, int* err,
+                                   cudaStream_t s) {
+  if (ncol < 1 || ncol > 256) throw DeviceError{cudaErrorInvalidValue};
+  const int np = (ncol + 15) / 16 * 16;
+  int kchunk = 0;
+  const int splits = tc_split_count(N, ncol, ws_bytes, &kchunk);
+  dim3 grid((N + kTcBM - 1) / kTcBM, splits);
   count_launches(1);
-  tc_gather_gemm_kernel<<<grid, kTcThreads, smem, s>>>(N, ncol, np, kchunk, G, U, idx, w, gscale,
-                                                       Y, static_cast<float*>(ws), err);
+  tc_gather_gemm_kernel<<<grid, kTcThreads, tc_smem_bytes(np), s>>>(
+      N, ncol, np, kchunk, G, U, idx, w, gscale, Y, static_cast<float*>(ws), err);
   MDS_CUDA(cudaGetLastError());
   return splits;
 }

@@ -49,3 +49,48 @@ def test_q80_eval_and_hessvec(big, p, ctx_prec):
         assert relerr(HU.cpu().numpy(), H_ref) <= 5e-5
     finally:
         mds.manidsdp_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def sparse120():
+    """The sparse-Q workload: q = 120, 5% Bernoulli support on the upper triangle
+    (N = 7261, m = 8,502,671); index map and b bit-exact against the oracle."""
+    inst = instance(120, seed=0, density=0.05)
+    assert inst["N"] == 7261 and inst["m"] == 8502671
+    assert np.array_equal(inst["idx"], inst["prob"]["idx"])
+    assert np.array_equal(inst["b"], inst["prob"]["b"])
+    return inst
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_q120_sparse_eval_and_hessvec(sparse120, engine):
+    """Psi, grad, z (df64, 1e-12) and the mixed Hess-vec (5e-5) with both gather-GEMM
+    engines at N = 7261: the largest index map of the workloads (211 MB)."""
+    torch = torch_cuda()
+    inst = sparse120
+    prob = inst["prob"]
+    p = 16
+    Y, Xt, U = random_state(inst, p, seed=7, xt_scale=0.02)
+    sigma = 2.0
+    prm = mds.manidsdp_default_params()
+    prm.precision_mode = mds.PREC_MIXED
+    prm.tensor_cores = engine
+    ctx = mds.manidsdp_setup(inst["N"], inst["m"], inst["idx"], inst["b"], params=prm)
+    try:
+        mds.manidsdp_set_state(ctx, Xt, sigma)
+        Yd = torch.tensor(Y, device="cuda"); Ud = torch.tensor(U, device="cuda")
+        g = torch.empty_like(Yd)
+        z = torch.empty(inst["N"], dtype=torch.float64, device="cuda")
+        psi, rn = mds.manidsdp_subproblem_eval(ctx, Yd, p, g, z)
+        G = sp.egrad_S(Y, prob, Xt, sigma)
+        psi_ref = sp.cost(Y, prob, Xt, sigma)
+        assert abs(psi - psi_ref) <= 1e-12 * abs(psi_ref)
+        assert relerr(g.cpu().numpy(), sp.proj_tangent(Y, 2 * G @ Y)) <= 1e-12
+        assert relerr(z.cpu().numpy(), sp.rowdot(G @ Y, Y)) <= 1e-12
+        HU = torch.empty_like(Yd)
+        mds.manidsdp_hessvec(ctx, Yd, Ud, p, HU, mds.PREC_MIXED)
+        err = relerr(HU.cpu().numpy(), sp.rhess(Y, U, prob, Xt, sigma, G))
+        print(f"q=120 engine={engine}: Hess-vec relative error {err:.2e}")
+        assert err <= 5e-5
+    finally:
+        mds.manidsdp_destroy(ctx)

@@ -1,12 +1,12 @@
 """The tensor-core gather GEMM of the FP32 Hessian-vector product
 (params.tensor_cores = 1: tcgen05 kind::tf32 with each operand split into two
-TF32 halves) against the FP64 oracle (Proposition 4.2, Eq. (4.7)) and against
+TF32 halves, four products per step) against the FP64 oracle (Proposition 4.2, Eq. (4.7)) and against
 the FP32 FMA kernel, through the C ABI.
 
 Tolerances: the mixed-form Hessian-vector product's 5e-5 relative against the
-oracle, for both FP32 engines and between them (the split leaves about 2^-21
-relative error per product against FP32's 2^-24, and the products cancel in
-Eq. (4.7), so the engines differ by ~1e-5 at N = 3241).  A solve with the tensor-core
+oracle, for both FP32 engines and between them (the split represents each
+operand to 2^-23, about FP32's own accuracy, but the sums of 2N products cancel
+in Eq. (4.7), so the engines differ by ~1e-5 at N = 3241).  A solve with the tensor-core
 engine meets the solver bar: eta_max <= 1e-8, value within 1e-9 of the oracle.
 """
 import numpy as np
