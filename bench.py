@@ -63,7 +63,8 @@ HV_TRAFFIC = {
     "fma": {"p": 51, "bytes": 191.1e6, "current": False,
             "note": "captured before the FP32 Gram moved to 32-row splits on a side stream"},
     "tc": {"p": 51, "bytes": 183.4e6, "current": False,
-           "note": "captured before the tensor-core kernel drained its accumulator in chains"},
+           "note": "captured before the tensor-core kernel rounded both TF32 halves and issued "
+                   "four products per step (same loads)"},
 }
 
 
@@ -76,7 +77,7 @@ def parse():
     ap.add_argument("--q", type=int, default=80)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--engine", choices=["fma", "tc"], default="fma",
+    ap.add_argument("--engine", choices=["fma", "tc"], default="tc",
                     help="gather GEMM of the FP32 Hessian-vector product: FP32 FMA kernel or "
                          "tensor cores (tcgen05 kind::tf32, two-term TF32 operand split)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)

@@ -15,7 +15,7 @@
 // lo*lo + lo*hi + hi*lo + hi*hi per K step of 8 (smallest first; about 2^-22
 // relative error per product, FP32 accumulation in tensor memory) and commits
 // them to an mbarrier; two shared-memory stages let the next chunk's loads and
-// stores overlap the running MMAs.  Every 8 chunks, and at the end, the
+// stores overlap the running MMAs.  Every 20 chunks, and at the end, the
 // accumulator (128 lanes x p columns of FP32 in TMEM) is read back with
 // tcgen05.ld by the four warps whose lane quarters cover the 128 rows and added
 // into the CTA's partial product in global memory.
@@ -36,11 +36,12 @@ constexpr int kTcThreads = 256;
 constexpr int kTcATile = kTcBM * 2 * kTcG * 4;  // bytes of one 128 x 32 FP32 operand tile
 constexpr long long kTcSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
 // Chunks accumulated in tensor memory before the accumulator is added into the
-// partial product in global memory (FP32, round to nearest): 8 chunks = 256 K
-// values per accumulation chain.  The tensor core's own FP32 accumulation loses
+// partial product in global memory (FP32, round to nearest): 20 chunks = 640 K
+// values per accumulation chain (at N = 3241 a split holds 19 chunks, so the
+// drain only runs for larger N, where each drain costs ~20 us of pipeline stall).  The tensor core's own FP32 accumulation loses
 // accuracy in proportion to the chain length (measured: 1.3e-5 relative Hess-vec
 // error with 590-term chains at N = 3241, 9.5e-5 with 2906-term chains at N = 7261).
-constexpr int kTcDrain = 8;
+constexpr int kTcDrain = 20;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
