@@ -159,6 +159,39 @@ class ClockSampler:
         return out
 
 
+def bench_config(args, world):
+    """The workload description shared by both arms."""
+    q = args.q
+    N = 1 + q + q * (q - 1) // 2
+    m = sum(math.comb(q, d) for d in range(5))
+    return {"workload": f"dense BQP order-2 moment relaxation, q={q}, seed={args.seed}",
+            "N": N, "m": m, "p0": int(math.ceil(math.log(m))), "precision": args.precision,
+            "hessvec_gemm": ("tensor cores (tcgen05 kind::tf32, operands split into two TF32 "
+                             "halves)" if args.engine == "tc" else "FP32 FMA"),
+            "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
+            "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",
+            "parallelism": f"replicas{world}"}
+
+
+def reduce_over_ranks(ms, steps_done, world, device):
+    """Replicas: the job's timed-region length is the slowest rank's, and its
+    work is the sum of the outer iterations all ranks completed."""
+    if world <= 1:
+        return ms, steps_done
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([steps_done], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(n.item()))
+
+
+def job_value(ms_max, total_steps):
+    """Seconds per outer iteration of the whole job."""
+    return ms_max / 1e3 / max(1, total_steps)
+
+
 def workload(q, seed):
     import paper_2512_04406_gb300 as mds
     from synthetic import bqp_instance
@@ -268,8 +301,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded N(0,1) Q, c)",
-        "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
-                   "N": 1 + args.q + args.q * (args.q - 1) // 2},
+        "config": bench_config(args, world),
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -337,13 +369,10 @@ def main():
     torch.cuda.synchronize()
     launches = mds.manidsdp_launch_count() - l0
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     clk = clocks.stop()
     steps_done = max(1, rep.outer)
-    value = ms / 1e3 / (steps_done * world)
+    ms, total_steps = reduce_over_ranks(ms, steps_done, world, "cuda")
+    value = job_value(ms, total_steps)
 
     # dominant kernel: the Hessian-vector product, live (phase events inside the
     # timed solves) and in isolation at p = p_0
@@ -458,13 +487,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/f64 (FP32 Hessian-vector products, FP64 elsewhere)" if prec == mds.PREC_MIXED else "f64",
             "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
-            "config": {"workload": f"dense BQP order-2 moment relaxation, q={args.q}, seed={args.seed}",
-                       "N": N, "m": m, "p0": p0, "precision": args.precision,
-                       "hessvec_gemm": "tensor cores (tcgen05 kind::tf32, operands split into two TF32 halves)" if args.engine == "tc"
-                       else "FP32 FMA",
-                       "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
-                       "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",
-                       "parallelism": f"replicas{world}"},
+            "config": bench_config(args, world),
             "steps_done": steps_done, "eta_max_after": rep.eta_max, "value_after": rep.value,
             "outer_total": args.warmup + rep.outer, "full_solve": solve60,
             "rtr_iters": rep.rtr_iters, "hessvecs": rep.hessvecs, "p_final": rep.p,

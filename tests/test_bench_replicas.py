@@ -1,0 +1,67 @@
+"""Host logic of bench.py's multi-GPU mode (replicas: one solve per rank, no
+collective on the data path) on CPU: two gloo ranks reduce their timings the
+way the GPU ranks do (max of the timed-region lengths, sum of the completed
+outer iterations), and the reference arm prints from rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, steps = bench.reduce_over_ranks(10.0 + rank, 4 - rank, world, "cpu")
+        out[rank] = (ms, steps, bench.job_value(ms, steps))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_like_the_gpu_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    # the slowest rank's 11 ms over 4 + 3 outer iterations
+    for r in range(2):
+        assert res[r][0] == 11.0 and res[r][1] == 7
+        assert res[r][2] == pytest.approx(11.0e-3 / 7)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_over_ranks(5.0, 3, 1, "cpu") == (5.0, 3)
+    assert bench.job_value(6.0, 3) == pytest.approx(2e-3)
+
+
+def test_reference_arm_prints_from_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
