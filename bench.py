@@ -53,7 +53,7 @@ UNIT = "s/ALM-outer-iteration"
 # steps of a GPU run), used to scale the sampled oracle timings to one outer
 # iteration when no GPU run precedes them.  The GPU arm uses the counts of its
 # own timed steps.
-DEFAULT_COUNTS = dict(hessvecs=7035, evals=166, grads=170, lanczos_matvecs=122, p=51)
+DEFAULT_COUNTS = dict(hessvecs=6622, evals=164, grads=170, lanczos_matvecs=115, p=49)
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one
 # Hess-vec) from one ncu capture at q = 80 and the p of the timed steps, per gather-GEMM
