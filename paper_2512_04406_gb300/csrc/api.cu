@@ -596,6 +596,18 @@ void default_params(manidsdp_params* p) {
   p->tensor_cores = 0;
 }
 
+// Ranges of the parameters (the switches are 0 or 1).
+bool params_ok(const manidsdp_params& p) {
+  auto flag = [](int32_t v) { return v == 0 || v == 1; };
+  return p.p_max >= 1 && p.p_max <= 256 && p.p0 >= 1 && p.p0 <= p.p_max && p.p_min >= 1 &&
+         p.delta_max >= 0 && p.lanczos_k >= 1 && p.max_outer >= 0 && p.max_rtr >= 0 &&
+         p.max_tcg >= 1 && p.carry_halvings >= 0 &&
+         (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
+         flag(p.tcg_device) && flag(p.warm_start) && flag(p.tensor_cores) &&
+         p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
+         p.tol > 0.0;
+}
+
 struct NonFinite {};
 
 int guard(const std::function<int()>& f) {
@@ -697,9 +709,7 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     prm = *params;
   else
     default_params(&prm);
-  if (prm.p_max < 1 || prm.p_max > 256 || prm.p0 < 1 || prm.p0 > prm.p_max || prm.p_min < 1 ||
-      prm.delta_max < 0 || prm.lanczos_k < 1)
-    return MANIDSDP_E_ARG;
+  if (!params_ok(prm)) return MANIDSDP_E_ARG;
   // validate the index map and build the per-class inverse map on the host
   const size_t NN = size_t(N) * N;
   std::vector<int32_t> count(m, 0);
@@ -881,8 +891,7 @@ void manidsdp_destroy(manidsdp_ctx* ctx) {
 }
 
 int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
-  if (c == nullptr || prm == nullptr || prm->p_max != c->prm.p_max || prm->p0 < 1 ||
-      prm->p0 > prm->p_max || prm->p_min < 1 || prm->delta_max < 0 || prm->lanczos_k < 1 ||
+  if (c == nullptr || prm == nullptr || !params_ok(*prm) || prm->p_max != c->prm.p_max ||
       prm->precision_mode != c->prm.precision_mode)
     return MANIDSDP_E_ARG;
   const bool engine_changed = prm->tensor_cores != c->prm.tensor_cores;

@@ -71,6 +71,18 @@ def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
         mds.manidsdp_setup(N, m + 1, idx, np.zeros(m + 1))
 
 
+@pytest.mark.parametrize("field,value", [("tensor_cores", 2), ("precision_mode", 5),
+                                         ("tcg_device", -1), ("warm_start", 3), ("gamma", 1.0),
+                                         ("p_max", 257), ("max_tcg", 0), ("sigma0", 0.0)])
+def test_setup_rejects_out_of_range_params_before_touching_the_gpu(field, value):
+    N, m, idx = mds.manidsdp_bqp_index_map(3, 2)
+    prm = mds.manidsdp_default_params()
+    setattr(prm, field, value)
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_setup(N, m, idx, np.zeros(m), params=prm)
+    assert e.value.status == mds.E_ARG
+
+
 @pytest.mark.parametrize("q", [1, 2, 3, 5, 8])
 def test_ucqp_index_map_and_rhs_bit_exact_vs_oracle(q):
     from oracle import ucqp
