@@ -93,6 +93,9 @@ def parse():
                          "(same kernels; for profilers that list kernels one launch at a time)")
     ap.add_argument("--hv-only", type=int, default=0,
                     help="only time the Hessian-vector product at this p (profiling)")
+    ap.add_argument("--hv-stages", action="store_true",
+                    help="with --hv-only: per-stage CUDA events (params.profile = 2, which "
+                         "serialises the side stream) and the mean time of each stage")
     return ap.parse_args()
 
 
@@ -328,7 +331,7 @@ def main():
     prm = mds.manidsdp_default_params()
     prm.precision_mode = prec
     prm.p_max = 256
-    prm.profile = 1
+    prm.profile = 2 if (args.hv_only and args.hv_stages) else 1
     prm.tensor_cores = 1 if args.engine == "tc" else 0
     if args.tcg_host:
         prm.tcg_device = 0
@@ -336,13 +339,19 @@ def main():
     ctx = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
     if args.hv_only:
         p = args.hv_only
+        mds.manidsdp_hessvec_stage_ms(ctx, True)
         ms = measure_hessvec(mds, torch, ctx, N, p, args.hv_reps, prec)
+        stages = mds.manidsdp_hessvec_stage_ms(ctx, True)
+        calls = args.hv_reps + 3  # measure_hessvec's warm-up calls are staged too
         fp_bytes = 4 if prec == mds.PREC_MIXED else 8
         byt = hessvec_bytes(N, m, N * (N + 1) // 2, m, p, fp_bytes)
-        print(json.dumps({"hv_only": True, "q": args.q, "N": N, "p": p, "precision": args.precision,
-                          "engine": args.engine,
-                          "ms": ms, "gbs": byt / (ms * 1e-3) / 1e9,
-                          "tflops": 6.0 * N * N * p / (ms * 1e-3) / 1e12}), flush=True)
+        out = {"hv_only": True, "q": args.q, "N": N, "p": p, "precision": args.precision,
+               "engine": args.engine,
+               "ms": ms, "gbs": byt / (ms * 1e-3) / 1e9,
+               "tflops": 6.0 * N * N * p / (ms * 1e-3) / 1e12}
+        if args.hv_stages:
+            out["stages_us"] = {k: round(v / calls * 1e3, 1) for k, v in stages.items()}
+        print(json.dumps(out), flush=True)
         mds.manidsdp_destroy(ctx)
         return
     Y0 = torch.tensor(gaussian_factor(N, p0, args.seed + rank), device="cuda")
