@@ -57,6 +57,18 @@ def test_bqp_rhs_bit_exact_vs_oracle(q, order):
     assert np.array_equal(b, ref)
 
 
+@pytest.mark.parametrize("q,density", [(80, None), (120, 0.05)])
+def test_workload_index_maps_and_rhs_bit_exact_vs_oracle(q, density):
+    """The benchmark's dense q = 80 map (N = 3241) and the sparse-Q q = 120 map
+    (N = 7261), with their right-hand sides, on the host."""
+    from synthetic import bqp_instance
+    N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
+    assert (N, m) == (1 + q + q * (q - 1) // 2, moment.num_monomials(q, 2))
+    assert np.array_equal(idx, moment.index_map(q, 2))
+    Q, c = bqp_instance(q, 0, density)
+    assert np.array_equal(mds.manidsdp_bqp_rhs(q, Q, c, 2), moment.rhs(q, Q, c, 2))
+
+
 def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
     N, m, idx = mds.manidsdp_bqp_index_map(3, 2)
     b = np.zeros(m)
