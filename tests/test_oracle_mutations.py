@@ -68,3 +68,31 @@ def test_missing_factor_two_in_rhs_caught():
     x = np.array([1.0, -1.0, 1.0, 1.0, -1.0])
     mv = np.array([np.prod(x[list(s)]) for s in monos])
     assert abs(b @ mv - moment.bqp_objective(x, Q, c)) > 1e-3
+
+
+def complex_hess_fd_error(hess_fn):
+    from oracle import ucqp_complex as uc
+    from synthetic import ucqp_instance
+    Q = ucqp_instance(8, 2)
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((8, 3)) + 1j * rng.standard_normal((8, 3))
+    Y /= np.linalg.norm(Y, axis=1)[:, None]
+    U = uc.proj_tangent(Y, rng.standard_normal((8, 3)) + 1j * rng.standard_normal((8, 3)))
+    t = 1e-5
+    fd = uc.proj_tangent(Y, (uc.rgrad(uc.retract(Y, t * U), Q)
+                             - uc.rgrad(uc.retract(Y, -t * U), Q)) / (2 * t))
+    H = hess_fn(Y, U, Q)
+    return np.abs(fd - H).max() / np.abs(H).max()
+
+
+def test_complex_hessian_pins_catch_a_dropped_weingarten_term_and_a_conjugation():
+    from oracle import ucqp_complex as uc
+    assert complex_hess_fd_error(uc.rhess) < 1e-6
+
+    def no_weingarten(Y, U, Q):
+        return uc.proj_tangent(Y, 2.0 * (Q @ U))
+    assert complex_hess_fd_error(no_weingarten) > 1e-3
+
+    def conjugated(Y, U, Q):  # Q^T in place of the Hermitian Q
+        return uc.proj_tangent(Y, 2.0 * (Q.T @ U)) - 2.0 * uc.multipliers(Y, Q)[:, None] * U
+    assert complex_hess_fd_error(conjugated) > 1e-3
