@@ -106,3 +106,19 @@ def test_ucqp_index_map_and_rhs_bit_exact_vs_oracle(q):
     Q = rng.standard_normal((q, q)); Q = Q + Q.T
     c = rng.standard_normal(q)
     assert np.array_equal(mds.manidsdp_ucqp_rhs(q, Q, c), ucqp.rhs(q, Q, c, classes))
+
+
+def test_noalloc_lanczos_rejects_sizes_and_arguments_before_touching_the_gpu():
+    """The no-alloc certificate check validates its sizes against the static
+    scratch (N <= 16384, k <= 256, k N <= 524288) and its arguments before any
+    CUDA call, so these return on a machine without a GPU."""
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((16385, 1)), None, mds.EIG_MIN, 4)
+    assert e.value.status == mds.E_TOOLARGE
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4096, 1)), None, mds.EIG_MIN, 129)
+    assert e.value.status == mds.E_TOOLARGE
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4, 4)), None, 7, 4)
+    assert e.value.status == mds.E_ARG
+    assert "scratch" in mds.manidsdp_strerror(mds.E_TOOLARGE)
