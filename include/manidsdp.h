@@ -313,6 +313,34 @@ int manidsdp_ucqp_index_map(int32_t q, int32_t* N, int64_t* m, int32_t* idx);
  * coefficients of delta and -delta.  Q: host q x q real symmetric; c: host q or NULL. */
 int manidsdp_ucqp_rhs(int32_t q, const double* Q, const double* c, double* b);
 
+/*
+ * manidsdp_sparse_bqp_index_map - host helper: the second-order relaxation of a
+ * sparse BQP with overlapping variable blocks (Section 6, sparse BQPs):
+ * min sum_k x_k'Q_k x_k + c_k'x_k over x in {-1,1}^{(q-2)t+2}, block k (0-based)
+ * holding the q variables (q-2)k .. (q-2)k+q-1.  The multi-block moment matrix
+ * (t blocks of order n_b = 1 + q + q(q-1)/2) is embedded in one symmetric matrix of
+ * order N = t n_b whose diagonal blocks carry the monomial classes (a square-free
+ * monomial of degree <= 4 inside one block, ordered by degree and then
+ * lexicographically on the sorted variables; *m_mono of them) and whose every
+ * off-block pair {(r,c), (c,r)} is a class of its own (numbered after the
+ * monomials, row-major in r < c; right-hand side 0).  The embedding has the
+ * optimal value of the multi-block relaxation: a block-diagonal solution
+ * extended by zeros is feasible for it, and the diagonal blocks of any of its
+ * solutions are feasible for the block problem with the same objective.
+ * q >= 2, t >= 1, N <= 65535.  Pass idx = NULL to query the sizes.
+ * idx: host N x N int32 output.  m_mono may be NULL.
+ */
+int manidsdp_sparse_bqp_index_map(int32_t q, int32_t t, int32_t* N, int64_t* m,
+                                  int64_t* m_mono, int32_t* idx);
+
+/* Right-hand side b (host, m FP64 output) of the sparse BQP relaxation: the
+ * coefficients of the objective modulo x_i^2 = 1 on the monomial classes (the
+ * constant: the traces of the Q_k summed block by block; x_i: the c_k entries;
+ * x_i x_j: Q_k[i][j] + Q_k[j][i], summed over the blocks sharing the monomial in
+ * block order), 0 on the off-block classes.  Qs: host t x q x q row-major (each
+ * symmetric); cs: host t x q or NULL. */
+int manidsdp_sparse_bqp_rhs(int32_t q, int32_t t, const double* Qs, const double* cs, double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,11 @@ _sig = {
     "manidsdp_ucqp_index_map": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int64), _P]),
     "manidsdp_ucqp_rhs": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P]),
+    "manidsdp_sparse_bqp_index_map": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(ctypes.c_int64),
+                                                     ctypes.POINTER(ctypes.c_int64), _P]),
+    "manidsdp_sparse_bqp_rhs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "manidsdp_lanczos_dense_noalloc": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_int32,
                                                       ctypes.c_int32,
                                                       ctypes.POINTER(ctypes.c_double), _P,
@@ -278,6 +283,39 @@ def manidsdp_bqp_rhs(q: int, Q, c=None, order: int = 2) -> np.ndarray:
     _check(_lib.manidsdp_bqp_rhs(q, order, _ptr(Q), _ptr(c), _ptr(b, np.float64, True)),
            "manidsdp_bqp_rhs")
     return b
+
+
+def manidsdp_sparse_bqp_index_map(q: int, t: int):
+    """Returns (N, m, m_mono, idx[N, N] int32) of the embedded multi-block relaxation
+    of a sparse BQP with t overlapping blocks of q variables."""
+    N, m, mm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.manidsdp_sparse_bqp_index_map(q, t, ctypes.byref(N), ctypes.byref(m),
+                                              ctypes.byref(mm), None),
+           "manidsdp_sparse_bqp_index_map")
+    idx = np.empty((N.value, N.value), dtype=np.int32)
+    _check(_lib.manidsdp_sparse_bqp_index_map(q, t, ctypes.byref(N), ctypes.byref(m),
+                                              ctypes.byref(mm), _ptr(idx, np.int32, True)),
+           "manidsdp_sparse_bqp_index_map")
+    return N.value, m.value, mm.value, idx
+
+
+def manidsdp_sparse_bqp_rhs(q: int, t: int, Qs, cs=None):
+    """b (m FP64) for the blocks' Q_k (t x q x q) and c_k (t x q)."""
+    _, m, _ = _sparse_sizes(q, t)
+    Qa = np.ascontiguousarray(np.asarray(Qs, dtype=np.float64).reshape(t, q, q))
+    ca = None if cs is None else np.ascontiguousarray(np.asarray(cs, dtype=np.float64).reshape(t, q))
+    b = np.empty(m)
+    _check(_lib.manidsdp_sparse_bqp_rhs(q, t, _ptr(Qa), _ptr(ca), _ptr(b, np.float64, True)),
+           "manidsdp_sparse_bqp_rhs")
+    return b
+
+
+def _sparse_sizes(q: int, t: int):
+    N, m, mm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.manidsdp_sparse_bqp_index_map(q, t, ctypes.byref(N), ctypes.byref(m),
+                                              ctypes.byref(mm), None),
+           "manidsdp_sparse_bqp_index_map")
+    return N.value, m.value, mm.value
 
 
 def manidsdp_ucqp_index_map(q: int):

@@ -261,3 +261,139 @@ extern "C" int manidsdp_ucqp_rhs(int32_t q, const double* Q, const double* c, do
     }
   return MANIDSDP_OK;
 }
+
+// ---- sparse BQP with overlapping variable blocks (Section 6, sparse BQPs) -------------
+// Block k holds the q consecutive variables (q-2)k .. (q-2)k+q-1 (0-based).  A monomial
+// class is a set of at most four variables inside one block; its key packs the degree
+// and the sorted variables (12 bits each), so sorting keys sorts by degree and then
+// lexicographically.  Entries outside the diagonal blocks of the stacked moment matrix
+// are classes of their own (one per unordered pair), numbered after the monomials in
+// row-major order of (r < c).
+namespace {
+
+uint64_t mono_key(int d, const int* v) {
+  uint64_t k = uint64_t(d);
+  for (int s = 0; s < 4; ++s) k = (k << 12) | uint64_t(s < d ? v[s] : 0);
+  return k;
+}
+
+struct SparseBqp {
+  int q = 0, t = 0, nb = 0, nvars = 0;
+  std::vector<uint64_t> keys;  // sorted monomial keys
+};
+
+bool sparse_bqp_layout(int q, int t, SparseBqp* L) {
+  if (q < 2 || t < 1) return false;
+  const int64_t nb = 1 + q + binom(q, 2);
+  const int64_t nvars = int64_t(q - 2) * t + 2;
+  if (nb * t > 65535 || nvars > 4095) return false;
+  L->q = q;
+  L->t = t;
+  L->nb = int(nb);
+  L->nvars = int(nvars);
+  L->keys.clear();
+  for (int k = 0; k < t; ++k) {
+    const int s0 = (q - 2) * k;
+    int v[4];
+    L->keys.push_back(mono_key(0, v));
+    for (int a = 0; a < q; ++a) {
+      v[0] = s0 + a;
+      L->keys.push_back(mono_key(1, v));
+      for (int b = a + 1; b < q; ++b) {
+        v[1] = s0 + b;
+        L->keys.push_back(mono_key(2, v));
+        for (int c = b + 1; c < q; ++c) {
+          v[2] = s0 + c;
+          L->keys.push_back(mono_key(3, v));
+          for (int e = c + 1; e < q; ++e) {
+            v[3] = s0 + e;
+            L->keys.push_back(mono_key(4, v));
+          }
+        }
+      }
+    }
+  }
+  std::sort(L->keys.begin(), L->keys.end());
+  L->keys.erase(std::unique(L->keys.begin(), L->keys.end()), L->keys.end());
+  return true;
+}
+
+int64_t mono_rank(const SparseBqp& L, const Mono& m) {
+  const uint64_t k = mono_key(m.d, m.v);
+  return std::lower_bound(L.keys.begin(), L.keys.end(), k) - L.keys.begin();
+}
+
+// Basis element a of block k: [1, x_i, x_i x_j (i < j)] over the block's variables.
+Mono block_basis_element(const SparseBqp& L, int k, int a) {
+  Mono m = basis_element(L.q, a);
+  for (int s = 0; s < m.d; ++s) m.v[s] += (L.q - 2) * k;
+  return m;
+}
+
+}  // namespace
+
+extern "C" int manidsdp_sparse_bqp_index_map(int32_t q, int32_t t, int32_t* N_out, int64_t* m_out,
+                                             int64_t* m_mono_out, int32_t* idx) {
+  if (N_out == nullptr || m_out == nullptr) return MANIDSDP_E_ARG;
+  SparseBqp L;
+  if (!sparse_bqp_layout(q, t, &L)) return MANIDSDP_E_ARG;
+  const int64_t N = int64_t(L.nb) * t;
+  const int64_t m_mono = int64_t(L.keys.size());
+  const int64_t m = m_mono + (N * N - int64_t(L.nb) * L.nb * t) / 2;
+  if (m > INT32_MAX) return MANIDSDP_E_ARG;
+  *N_out = int32_t(N);
+  *m_out = m;
+  if (m_mono_out) *m_mono_out = m_mono;
+  if (idx == nullptr) return MANIDSDP_OK;
+  for (int k = 0; k < t; ++k) {
+    const int64_t o = int64_t(k) * L.nb;
+    for (int a = 0; a < L.nb; ++a) {
+      const Mono ba = block_basis_element(L, k, a);
+      for (int g = 0; g < L.nb; ++g) {
+        const Mono s = xor_sets(ba, block_basis_element(L, k, g));
+        idx[(o + a) * N + o + g] = int32_t(mono_rank(L, s));
+      }
+    }
+  }
+  int64_t next = m_mono;
+  for (int64_t r = 0; r < N; ++r)
+    for (int64_t c = r + 1; c < N; ++c)
+      if (r / L.nb != c / L.nb) {
+        idx[r * N + c] = int32_t(next);
+        idx[c * N + r] = int32_t(next);
+        ++next;
+      }
+  return MANIDSDP_OK;
+}
+
+extern "C" int manidsdp_sparse_bqp_rhs(int32_t q, int32_t t, const double* Qs, const double* cs,
+                                       double* b) {
+  if (Qs == nullptr || b == nullptr) return MANIDSDP_E_ARG;
+  SparseBqp L;
+  if (!sparse_bqp_layout(q, t, &L)) return MANIDSDP_E_ARG;
+  int32_t N;
+  int64_t m, m_mono;
+  const int st = manidsdp_sparse_bqp_index_map(q, t, &N, &m, &m_mono, nullptr);
+  if (st != MANIDSDP_OK) return st;
+  for (int64_t a = 0; a < m; ++a) b[a] = 0.0;
+  double tr = 0.0;
+  for (int k = 0; k < t; ++k) {
+    const double* Q = Qs + size_t(k) * q * q;
+    for (int i = 0; i < q; ++i) tr += Q[size_t(i) * q + i];
+    const int s0 = (q - 2) * k;
+    Mono m1{1, {0, 0, 0, 0}};
+    for (int i = 0; i < q; ++i) {
+      m1.v[0] = s0 + i;
+      b[mono_rank(L, m1)] += cs ? cs[size_t(k) * q + i] : 0.0;
+    }
+    Mono m2{2, {0, 0, 0, 0}};
+    for (int i = 0; i < q; ++i)
+      for (int j = i + 1; j < q; ++j) {
+        m2.v[0] = s0 + i;
+        m2.v[1] = s0 + j;
+        b[mono_rank(L, m2)] += Q[size_t(i) * q + j] + Q[size_t(j) * q + i];
+      }
+  }
+  b[0] = tr;  // x_i^2 = 1 turns the diagonals of the Q_k into one constant
+  return MANIDSDP_OK;
+}

@@ -45,6 +45,22 @@ def bqp_instance(q: int, seed: int, density: float | None = None):
     return Q, c
 
 
+def sparse_bqp_instance(q: int, t: int, seed: int):
+    """Return (Qs, cs) for the t blocks of a sparse BQP with overlapping variable
+    blocks: for each block in order, with one ``default_rng(seed)`` stream, the
+    upper triangle of Q_k including the diagonal, row-major, iid N(0,1) (mirrored),
+    then c_k, iid N(0,1)."""
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(q)
+    Qs, cs = [], []
+    for _ in range(t):
+        Q = np.zeros((q, q))
+        Q[iu] = rng.standard_normal(len(iu[0]))
+        Qs.append(Q + np.triu(Q, 1).T)
+        cs.append(rng.standard_normal(q))
+    return Qs, cs
+
+
 def ucqp_instance(n: int, seed: int):
     """Return a Hermitian complex Q (n x n): real and imaginary parts of the
     strict upper triangle iid N(0,1) (real parts drawn first, row-major), a real

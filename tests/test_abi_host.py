@@ -122,3 +122,17 @@ def test_noalloc_lanczos_rejects_sizes_and_arguments_before_touching_the_gpu():
         mds.manidsdp_lanczos_dense_noalloc(np.zeros((4, 4)), None, 7, 4)
     assert e.value.status == mds.E_ARG
     assert "scratch" in mds.manidsdp_strerror(mds.E_TOOLARGE)
+
+
+@pytest.mark.parametrize("q,t", [(2, 3), (3, 1), (4, 2), (5, 3), (8, 4), (20, 2)])
+def test_sparse_bqp_index_map_and_rhs_bit_exact_vs_oracle(q, t):
+    from oracle import multiblock as mb
+    from synthetic import sparse_bqp_instance
+    N, m, m_mono, idx = mds.manidsdp_sparse_bqp_index_map(q, t)
+    ref, nm = mb.index_map(q, t)
+    assert (N, m, m_mono) == (ref.shape[0], mb.num_classes(q, t), nm)
+    assert np.array_equal(idx, ref)
+    Qs, cs = sparse_bqp_instance(q, t, q + t)
+    assert np.array_equal(mds.manidsdp_sparse_bqp_rhs(q, t, Qs, cs), mb.rhs(q, t, Qs, cs))
+    assert np.array_equal(mds.manidsdp_sparse_bqp_rhs(q, t, Qs, None),
+                          mb.rhs(q, t, Qs, [np.zeros(q)] * t))
