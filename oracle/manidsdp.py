@@ -49,6 +49,7 @@ import math
 
 import numpy as np
 
+from . import direct as direct_mod
 from . import operators as ops
 from . import subproblem as sp
 from .lanczos import lanczos
@@ -108,7 +109,10 @@ def kkt_residuals(prob, y, S, X, z, lam_min, lam_max):
     return eta_p, eta_d, eta_g, pobj, dobj
 
 
-def solve(prob, Y0, params=None, eig="dense", history=None):
+def solve(prob, Y0, params=None, eig="dense", history=None, direct=False):
+    """Algorithm 1.  With direct=True each subproblem is the direct formulation's
+    (oracle/direct.py: y frozen at the previous y-update instead of y(S)); the
+    outer loop is otherwise the same."""
     prm = dict(DEFAULTS)
     if params:
         prm.update(params)
@@ -117,6 +121,7 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
     Cz = 0.0 if C is None else C
     Y = _rownorm(np.array(Y0, dtype=np.float64))
     p = Y.shape[1]
+    y_prev = ops.y_of(Y @ Y.T, C, idx, mult) if direct else None
     Xt = np.zeros((N, N))
     sigma = prm["sigma0"]
     U = None
@@ -125,11 +130,18 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
     totals = dict(rtr=0, hessvecs=0)
     result = None
     for k in range(prm["max_outer"]):
-        f = lambda Yv: sp.cost(Yv, prob, Xt, sigma)
+        if direct:
+            f = lambda Yv: direct_mod.cost(Yv, prob, Xt, sigma, y_prev)
+            egrad = lambda Yv: direct_mod.egrad_S(Yv, prob, Xt, sigma, y_prev)
+            rhess = lambda Yv, Uv, G: direct_mod.rhess(Yv, Uv, prob, Xt, sigma, y_prev, G)
+        else:
+            f = lambda Yv: sp.cost(Yv, prob, Xt, sigma)
+            egrad = lambda Yv: sp.egrad_S(Yv, prob, Xt, sigma)
+            rhess = lambda Yv, Uv, G: sp.rhess(Yv, Uv, prob, Xt, sigma, G)
         # step 3a: the carried direction
         if U is not None:
-            G0 = sp.egrad_S(Y, prob, Xt, sigma)
-            curv = float(np.sum(U * sp.rhess(Y, U, prob, Xt, sigma, G0)))
+            G0 = egrad(Y)
+            curv = float(np.sum(U * rhess(Y, U, G0)))
             moved = False
             if curv < 0.0:
                 f0 = f(Y)
@@ -151,13 +163,13 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
         Gcache = {}
 
         def grad(Yv):
-            G = sp.egrad_S(Yv, prob, Xt, sigma)
+            G = egrad(Yv)
             Gcache["Y"], Gcache["G"] = Yv, G
             return sp.proj_tangent(Yv, 2.0 * G @ Yv)
 
         def hess(Yv, Uv):
-            G = Gcache["G"] if Gcache.get("Y") is Yv else sp.egrad_S(Yv, prob, Xt, sigma)
-            return sp.rhess(Yv, Uv, prob, Xt, sigma, G)
+            G = Gcache["G"] if Gcache.get("Y") is Yv else egrad(Yv)
+            return rhess(Yv, Uv, G)
 
         Y, info = rtr(Y, f, grad, hess, sp.retract, Delta_bar, tol_k,
                       max_iter=prm["max_rtr"], max_tcg=prm["max_tcg"], tcg_floor=prm["tcg_floor"],
@@ -168,6 +180,7 @@ def solve(prob, Y0, params=None, eig="dense", history=None):
         # steps 4-8
         S = Y @ Y.T
         y = ops.y_of(S, C, idx, mult)
+        y_prev = y
         R = ops.Astar(y, idx) - S - Cz
         Xt = Xt - sigma * R
         z = sp.rowdot((Xt + D) @ Y, Y)
