@@ -28,19 +28,19 @@ from . import subproblem as sp
 
 def stale_residual(Y, prob, y_prev):
     """A*(y^k) - Z at the current Y."""
-    return ops.Astar(y_prev, prob["idx"]) - sp.Zmat(Y, prob)
+    return ops.Astar_prob(y_prev, prob) - sp.Zmat(Y, prob)
 
 
 def cost(Y, prob, W, sigma, y_prev) -> float:
     Z = sp.Zmat(Y, prob)
-    R = ops.Astar(y_prev, prob["idx"]) - Z
+    R = ops.Astar_prob(y_prev, prob) - Z
     return float(np.sum((prob["D"] + W) * Z) + 0.5 * sigma * np.sum(R * R))
 
 
 def lagrangian(Y, prob, Xbar, sigma, y) -> float:
     """The direct augmented Lagrangian L^_sigma(S, y, Xbar) of Eq.
     (direct-augmented-lagrangian), at S = Y Y'."""
-    R = ops.Astar(y, prob["idx"]) - sp.Zmat(Y, prob)
+    R = ops.Astar_prob(y, prob) - sp.Zmat(Y, prob)
     return float(prob["b"] @ y - np.sum(Xbar * R) + 0.5 * sigma * np.sum(R * R))
 
 

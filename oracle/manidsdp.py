@@ -66,7 +66,21 @@ DEFAULTS = dict(
 
 
 def make_problem(idx, mult, b, C=None):
-    return dict(idx=idx, mult=mult, b=b, C=C, D=ops.D_matrix(b, idx, mult))
+    return dict(idx=idx, mult=mult, b=b, C=C, D=ops.D_matrix(b, idx, mult), N=idx.shape[0])
+
+
+def make_problem_general(Amat, b, C=None):
+    """A general constraint operator: Amat is m x N^2, row i the vectorised
+    symmetric matrix A_i, so A(Z)_i = <A_i, Z> and A*(v) = sum_i v_i A_i.  A A*
+    is factored once by Cholesky (the remark after Algorithm 1); D = A*((A A*)^{-1} b)."""
+    from scipy.linalg import cho_factor, cho_solve
+    Amat = np.asarray(Amat, dtype=np.float64)
+    N = int(round(math.sqrt(Amat.shape[1])))
+    assert N * N == Amat.shape[1]
+    Mfac = cho_factor(Amat @ Amat.T)
+    D = (Amat.T @ cho_solve(Mfac, b)).reshape(N, N)
+    return dict(Amat=Amat, Mfac=Mfac, N=N, b=np.asarray(b, dtype=np.float64), C=C, D=D,
+                idx=None, mult=None)
 
 
 def _rownorm(Y):
@@ -99,7 +113,7 @@ def kkt_residuals(prob, y, S, X, z, lam_min, lam_max):
     """eta_p, eta_d, eta_g of Section 6."""
     C = prob["C"]
     Cz = 0.0 if C is None else C
-    R = ops.Astar(y, prob["idx"]) - S - Cz
+    R = ops.Astar_prob(y, prob) - S - Cz
     normC = 0.0 if C is None else float(np.linalg.norm(C))
     eta_p = float(np.linalg.norm(R)) / (1.0 + normC)
     eta_d = max(0.0, -lam_min) / (1.0 + abs(lam_max))
@@ -116,12 +130,12 @@ def solve(prob, Y0, params=None, eig="dense", history=None, direct=False):
     prm = dict(DEFAULTS)
     if params:
         prm.update(params)
-    idx, mult, b, C, D = prob["idx"], prob["mult"], prob["b"], prob["C"], prob["D"]
-    N = idx.shape[0]
+    b, C, D = prob["b"], prob["C"], prob["D"]
+    N = prob["N"]
     Cz = 0.0 if C is None else C
     Y = _rownorm(np.array(Y0, dtype=np.float64))
     p = Y.shape[1]
-    y_prev = ops.y_of(Y @ Y.T, C, idx, mult) if direct else None
+    y_prev = ops.y_prob(Y @ Y.T + Cz, prob) if direct else None
     Xt = np.zeros((N, N))
     sigma = prm["sigma0"]
     U = None
@@ -179,9 +193,9 @@ def solve(prob, Y0, params=None, eig="dense", history=None, direct=False):
         gnorm = info["gradnorm"]
         # steps 4-8
         S = Y @ Y.T
-        y = ops.y_of(S, C, idx, mult)
+        y = ops.y_prob(S if C is None else S + C, prob)
         y_prev = y
-        R = ops.Astar(y, idx) - S - Cz
+        R = ops.Astar_prob(y, prob) - S - Cz
         Xt = Xt - sigma * R
         z = sp.rowdot((Xt + D) @ Y, Y)
         X = Xt + D - np.diag(z)
@@ -203,8 +217,8 @@ def solve(prob, Y0, params=None, eig="dense", history=None, direct=False):
             Yr = np.sign(Y @ Wv_[:, -1])[:, None]
             Yr[Yr == 0] = 1.0
             Sr = Yr @ Yr.T
-            yr = ops.y_of(Sr, C, idx, mult)
-            Rr = ops.Astar(yr, idx) - Sr - Cz
+            yr = ops.y_prob(Sr if C is None else Sr + C, prob)
+            Rr = ops.Astar_prob(yr, prob) - Sr - Cz
             if np.abs(Rr).max() == 0.0:
                 zr = sp.rowdot((Xt + D) @ Yr, Yr)
                 Xr = Xt + D - np.diag(zr)

@@ -12,6 +12,7 @@ With A_alpha the 0/1 indicator of the entries mapped to monomial alpha:
 from __future__ import annotations
 
 import numpy as np
+from scipy.linalg import cho_solve
 
 
 def A(Z: np.ndarray, idx: np.ndarray, m: int) -> np.ndarray:
@@ -42,3 +43,27 @@ def Q(Z: np.ndarray, idx, mult) -> np.ndarray:
 
 def D_matrix(b: np.ndarray, idx, mult) -> np.ndarray:
     return Astar(b / mult, idx)
+
+
+# ---- the operators of a problem dict: 0/1 classes (idx, mult) or a general A ----
+# A general operator is held as the m x N^2 matrix Amat of the vectorised
+# constraint matrices, with the Cholesky factor Mfac of A A* computed once (the
+# remark after Algorithm 1: A A* is factored once and reused).
+
+def y_prob(Z: np.ndarray, prob) -> np.ndarray:
+    """(A A*)^{-1} A(Z)."""
+    if prob.get("Amat") is not None:
+        return cho_solve(prob["Mfac"], prob["Amat"] @ Z.ravel())
+    return A(Z, prob["idx"], len(prob["mult"])) / prob["mult"]
+
+
+def Astar_prob(v: np.ndarray, prob) -> np.ndarray:
+    if prob.get("Amat") is not None:
+        N = prob["N"]
+        return (prob["Amat"].T @ v).reshape(N, N)
+    return Astar(v, prob["idx"])
+
+
+def Q_prob(Z: np.ndarray, prob) -> np.ndarray:
+    return Z - Astar_prob(y_prob(Z, prob), prob)
+

@@ -10,8 +10,9 @@ Hess Psi_k(Y)[U] = H - Diag(H Y') Y - 2 Diag(G S) U,
 Retraction (a reading: the paper names none; the oblique manifold's usual
 choice): Retr_Y(U) normalises each row of Y + U to unit length.
 
-Every function takes the data as a dict ``prob`` with keys idx, mult, b, C
-(None for C = 0), D and the ALM state Xt, sigma.
+Every function takes the data as a dict ``prob`` with keys b, C (None for
+C = 0), D and the constraint operator (idx, mult for 0/1 classes, or Amat and
+the factor Mfac of A A* for a general A), and the ALM state Xt, sigma.
 """
 from __future__ import annotations
 
@@ -42,15 +43,15 @@ def Zmat(Y, prob):
 def residual(Y, prob):
     """R = A*(y(S)) - S - C = -Q(S + C)  (Eq. (projected-y)) and y(S)."""
     Z = Zmat(Y, prob)
-    y = ops.A(Z, prob["idx"], len(prob["mult"])) / prob["mult"]
-    R = ops.Astar(y, prob["idx"]) - Z
+    y = ops.y_prob(Z, prob)
+    R = ops.Astar_prob(y, prob) - Z
     return R, y
 
 
 def cost(Y, prob, Xt, sigma) -> float:
     """Psi_k(Y) written as <D + Xt, Z> + sigma/2 ||Q(Z)||^2."""
     Z = Zmat(Y, prob)
-    QZ = ops.Q(Z, prob["idx"], prob["mult"])
+    QZ = ops.Q_prob(Z, prob)
     return float(np.sum((prob["D"] + Xt) * Z) + 0.5 * sigma * np.sum(QZ * QZ))
 
 
@@ -59,8 +60,8 @@ def cost_lagrangian(Y, prob, Xt, sigma) -> float:
     statement of the same function, used as a pin)."""
     S = Y @ Y.T
     C = 0.0 if prob["C"] is None else prob["C"]
-    y = ops.y_of(S, prob["C"], prob["idx"], prob["mult"])
-    Ay = ops.Astar(y, prob["idx"])
+    y = ops.y_prob(S if prob["C"] is None else S + prob["C"], prob)
+    Ay = ops.Astar_prob(y, prob)
     Rr = Ay - S - C
     return float(prob["b"] @ y - np.sum(Xt * Rr) + 0.5 * sigma * np.sum(Rr * Rr))
 
@@ -95,7 +96,7 @@ def ehess(Y, U, prob, Xt, sigma, G=None) -> np.ndarray:
     if G is None:
         G = egrad_S(Y, prob, Xt, sigma)
     W = Y @ U.T + U @ Y.T
-    return 2.0 * G @ U + 2.0 * sigma * ops.Q(W, prob["idx"], prob["mult"]) @ Y
+    return 2.0 * G @ U + 2.0 * sigma * ops.Q_prob(W, prob) @ Y
 
 
 def rhess(Y, U, prob, Xt, sigma, G=None) -> np.ndarray:
