@@ -2,8 +2,11 @@
 // Riemannian Hessian-vector product, Lanczos on the certificate, and
 // Algorithm 1 (ALM outer loop around Riemannian trust region with truncated CG).
 // The host here only sequences kernels and takes the scalar decisions (tCG step
-// sizes, trust-region ratio, sigma rule, rank update); every vector and matrix
-// operation runs in the kernels of kernels_seg.cu and kernels_dense.cu.
+// sizes when the loop is host-driven, trust-region ratio, sigma rule, rank
+// update); every vector and matrix operation runs in the kernels: kernels_seg.cu
+// and kernels_dense.cu (FP64 form), kernels_df64.cu (df64 evaluation),
+// kernels_sddmm.cu, kernels_gemm32.cu and kernels_tc.cu (FP32 Hessian-vector
+// product), kernels_tcg.cu (device-driven truncated CG).
 #include <algorithm>
 #include <chrono>
 #include <cstring>
