@@ -96,9 +96,7 @@ void launch_hv_epilogue(int N, int p, int splits, const T* part, const T* M, con
                         cudaStream_t s);
 // ---- df64 evaluation (kernels_df64.cu): FP64-accurate on the FP32 pipe ----
 void launch_split(size_t n, const double* x, float* hi, float* lo, cudaStream_t s);
-void launch_class_means_df(const ClassMap& cm, int N, int p, const float* Yh, const float* Yl,
-                           const double* C, const double* mult, double* piece_buf, double* out,
-                           cudaStream_t s);
+
 void launch_gpass_df(int N, int p, int mode, const float* Yh, const float* Yl,
                      const int32_t* idx, const double* y, const double* C, double sigma,
                      double* XD, double* G, float* Gh, float* Gl, double* part, double* out2,

@@ -29,43 +29,7 @@ void launch_split(size_t n, const double* x, float* hi, float* lo, cudaStream_t 
   MDS_CUDA(cudaGetLastError());
 }
 
-// ---- y(S): per-class means of S over the inverse map --------------------------------
-template <int LG>
-__global__ void __launch_bounds__(256) class_means_df_kernel(
-    int n_pieces, int N, int p, const uint32_t* __restrict__ ent,
-    const int32_t* __restrict__ piece_start, const int32_t* __restrict__ piece_class,
-    const float* __restrict__ Yh, const float* __restrict__ Yl, const double* __restrict__ C,
-    const double* __restrict__ mult, double* __restrict__ piece_buf, double* __restrict__ out) {
-  const int lane = threadIdx.x % LG;
-  const int piece = (blockIdx.x * blockDim.x + threadIdx.x) / LG;
-  const bool active = piece < n_pieces;
-  double acc = 0.0;
-  int cls = 0;
-  if (active) {
-    const int e0 = piece_start[piece], e1 = piece_start[piece + 1];
-    cls = piece_class[piece];
-    for (int e = e0; e < e1; ++e) {
-      const uint32_t code = ent[e];
-      const int b = int(code >> 16), g = int(code & 0xFFFFu);
-      const double wt = (b == g) ? 1.0 : 2.0;
-      const size_t ob = size_t(b) * p, og = size_t(g) * p;
-      df64acc a{0.f, 0.f};
-      for (int c = lane; c < p; c += LG) df64_fma(a, Yh[ob + c], Yl[ob + c], Yh[og + c], Yl[og + c]);
-      double v = df64_value(a);
-      if (C != nullptr && lane == 0) v += C[size_t(b) * N + g];
-      acc = fma(wt, v, acc);
-    }
-  }
-#pragma unroll
-  for (int off = LG / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (active && lane == 0) {
-    if (cls >= 0)
-      out[cls] = acc / mult[cls];
-    else
-      piece_buf[piece] = acc;
-  }
-}
-
+// ---- y(S): the multi-piece classes' sums of the per-piece df64 partials ------------
 __global__ void class_finalize_df_kernel(int n_multi, const int32_t* __restrict__ multi_class,
                                          const int32_t* __restrict__ multi_range,
                                          const double* __restrict__ piece_buf,
@@ -78,42 +42,6 @@ __global__ void class_finalize_df_kernel(int n_multi, const int32_t* __restrict_
   out[cls] = s / mult[cls];
 }
 
-template <int LG>
-static void means_df_lg(const ClassMap& cm, int N, int p, const float* Yh, const float* Yl,
-                        const double* C, const double* mult, double* piece_buf, double* out,
-                        cudaStream_t s) {
-  const long long lanes = (long long)cm.n_pieces * LG;
-  const int blocks = int((lanes + 255) / 256);
-  if (blocks > 0) {
-    count_launches(1);
-    class_means_df_kernel<LG><<<blocks, 256, 0, s>>>(cm.n_pieces, N, p, cm.ent, cm.piece_start,
-                                                     cm.piece_class, Yh, Yl, C, mult, piece_buf,
-                                                     out);
-  }
-  if (cm.n_multi > 0) {
-    count_launches(1);
-    class_finalize_df_kernel<<<(cm.n_multi + 255) / 256, 256, 0, s>>>(
-        cm.n_multi, cm.multi_class, cm.multi_range, piece_buf, mult, out);
-  }
-  MDS_CUDA(cudaGetLastError());
-}
-
-void launch_class_means_df(const ClassMap& cm, int N, int p, const float* Yh, const float* Yl,
-                           const double* C, const double* mult, double* piece_buf, double* out,
-                           cudaStream_t s) {
-  if (p <= 2)
-    means_df_lg<1>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-  else if (p <= 4)
-    means_df_lg<2>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-  else if (p <= 8)
-    means_df_lg<4>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-  else if (p <= 16)
-    means_df_lg<8>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-  else if (p <= 32)
-    means_df_lg<16>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-  else
-    means_df_lg<32>(cm, N, p, Yh, Yl, C, mult, piece_buf, out, s);
-}
 
 // ---- G pass (upper-triangle tiles, mirrored writes; see gpass_kernel) -------------------
 constexpr int DT = 64, DKC = 16;
