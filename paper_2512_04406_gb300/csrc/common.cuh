@@ -174,7 +174,6 @@ void launch_hess_epilogue(int N, int p, const T* Tm, const T* YM, const T* Y, co
                           const double* z, double sigma, double* HU, cudaStream_t s);
 
 // Row-local ops (FP64)
-void launch_proj_tangent(int N, int p, const double* Y, const double* U, double* out, cudaStream_t s);
 void launch_retract(int N, int p, const double* Y, const double* E, double t, double* out,
                     cudaStream_t s);  // rows of Y + t E normalised
 void launch_rowdot(int N, int p, const double* A, const double* B, double* out, cudaStream_t s);
@@ -182,7 +181,6 @@ void launch_rowdot(int N, int p, const double* A, const double* B, double* out, 
 void launch_grad_from_gy(int N, int p, const double* GY, const double* z, const double* Y,
                          double* grad, cudaStream_t s);
 void launch_to_float(size_t n, const double* a, float* out, cudaStream_t s);
-void launch_to_double(size_t n, const float* a, double* out, cudaStream_t s);
 // out = a*x + b*y (elementwise, n)
 void launch_axpby(size_t n, double a, const double* x, double b, const double* y, double* out,
                   cudaStream_t s);

@@ -500,12 +500,6 @@ __global__ void rowop_kernel(int N, int p, const double* __restrict__ Y,
   }
 }
 
-void launch_proj_tangent(int N, int p, const double* Y, const double* U, double* out,
-                         cudaStream_t s) {
-  count_launches(1);
-  rowop_kernel<0><<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, Y, U, 0.0, out);
-  MDS_CUDA(cudaGetLastError());
-}
 void launch_retract(int N, int p, const double* Y, const double* E, double t, double* out,
                     cudaStream_t s) {
   count_launches(1);
@@ -541,11 +535,6 @@ __global__ void to_float_kernel(size_t n, const double* __restrict__ a, float* _
        i += size_t(gridDim.x) * blockDim.x)
     o[i] = float(a[i]);
 }
-__global__ void to_double_kernel(size_t n, const float* __restrict__ a, double* __restrict__ o) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    o[i] = double(a[i]);
-}
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return int(b > 8192 ? 8192 : (b == 0 ? 1 : b));
@@ -553,11 +542,6 @@ static int grid_for(size_t n) {
 void launch_to_float(size_t n, const double* a, float* out, cudaStream_t s) {
   count_launches(1);
   to_float_kernel<<<grid_for(n), 256, 0, s>>>(n, a, out);
-  MDS_CUDA(cudaGetLastError());
-}
-void launch_to_double(size_t n, const float* a, double* out, cudaStream_t s) {
-  count_launches(1);
-  to_double_kernel<<<grid_for(n), 256, 0, s>>>(n, a, out);
   MDS_CUDA(cudaGetLastError());
 }
 
