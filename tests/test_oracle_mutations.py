@@ -96,3 +96,35 @@ def test_complex_hessian_pins_catch_a_dropped_weingarten_term_and_a_conjugation(
     def conjugated(Y, U, Q):  # Q^T in place of the Hermitian Q
         return uc.proj_tangent(Y, 2.0 * (Q.T @ U)) - 2.0 * uc.multipliers(Y, Q)[:, None] * U
     assert complex_hess_fd_error(conjugated) > 1e-3
+
+
+def test_multiblock_rhs_pin_catches_an_overwritten_shared_monomial():
+    """Blocks share two variables, so the monomials of those variables collect terms
+    from both blocks; overwriting instead of accumulating must break the pin that b
+    reproduces the objective."""
+    import math
+    from oracle import multiblock as mb
+    from synthetic import sparse_bqp_instance
+    q, t = 4, 3
+    Qs, cs = sparse_bqp_instance(q, t, 5)
+    mons = mb.monomials(q, t)
+    rank = {mono: r for r, mono in enumerate(mons)}
+
+    def bad_rhs():
+        b = np.array(mb.rhs(q, t, Qs, cs))
+        for k, vars_k in enumerate(mb.block_variables(q, t)):  # overwrite: last block wins
+            for i in range(q):
+                b[rank[(vars_k[i],)]] = cs[k][i]
+        return b
+
+    def max_error(b):
+        rng = np.random.default_rng(0)
+        err = 0.0
+        for _ in range(20):
+            x = rng.choice([-1.0, 1.0], mb.num_variables(q, t))
+            val = sum(b[a] * math.prod(x[i] for i in mono) for a, mono in enumerate(mons))
+            err = max(err, abs(val - mb.objective(x, q, t, Qs, cs)))
+        return err
+
+    assert max_error(mb.rhs(q, t, Qs, cs)) < 1e-10
+    assert max_error(bad_rhs()) > 1e-3
