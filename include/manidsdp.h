@@ -224,14 +224,14 @@ int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t whic
 /*
  * manidsdp_lanczos_dense_noalloc - extreme eigenpair of X - Diag(d) for a dense
  * symmetric matrix the caller already holds, without allocating device memory.
- * The paper has no counterpart: it is the certificate check of Algorithm 1
- * (steps 7-9, the same Lanczos iteration, stopping rules and sign convention as
- * manidsdp_lanczos) offered without a context, for callers that must not
- * allocate at the call site - e.g. a serving loop whose device memory is held
- * by a caching allocator (a cudaMalloc there can fail although the cache has
- * free blocks) or one that cannot take the device-wide synchronisation a
- * cudaFree implies.  Its Krylov basis lives in one static device array of the
- * library (4.4 MiB, reserved when the library's module loads on a device).
+ * The paper has no counterpart.  It computes what manidsdp_lanczos computes
+ * (Lanczos with full FP64 reorthogonalisation, the same start vector and sign
+ * convention), but without a context, for callers that cannot allocate at the
+ * call site: a serving loop whose device memory is held by a caching allocator
+ * (a cudaMalloc there can fail although the cache has free blocks), or code that
+ * cannot take the device-wide synchronisation a cudaFree implies.  Its Krylov
+ * basis lives in one static device array of the library (4.4 MiB, held by every
+ * device that loads the library until the process exits).
  *   N       order of X, 1 <= N <= 16384.
  *   X       device N x N FP64, row-major, symmetric (only read).  Must be
  *           readable by the current device: its device memory, managed memory
@@ -246,15 +246,19 @@ int manidsdp_lanczos(manidsdp_ctx* ctx, const double* Y, int32_t p, int32_t whic
  *           entry above 1e-14 in magnitude positive (may be NULL).
  *   steps   host, may be NULL.  stream: cudaStream_t as void* (NULL = legacy
  *           default stream); it must belong to the current device.
+ * Stopping: every 10 steps, when the Ritz pair at the requested end has a
+ * residual below 1e-10 and the one at the other end below 1e-6 (relative to the
+ * larger extreme Ritz value), or after k steps.
  * The call returns after its work on the stream has finished.  Nothing in the
  * scratch needs to be zero beforehand: each call clears what it accumulates.
  * Calls on the same device share the scratch: two calls in flight at the same
  * time on one device (two streams or two host threads) corrupt each other, so
- * serialise them.  The first call on each device looks up the scratch address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture begins on the device.
+ * serialise them.  Each call looks up the scratch's device address with
+ * cudaGetSymbolAddress in the current context; the first call on a device also
+ * loads the library's module there, so make that first call before any stream
+ * capture begins on the device.
  * Errors: E_ARG (bad arguments), E_TOOLARGE (limits above), E_NONFINITE,
- * E_CUDA (a CUDA call failed; the scratch lookup is retried on the next call).
+ * E_CUDA (a CUDA call failed).
  */
 int manidsdp_lanczos_dense_noalloc(int32_t N, const double* X, const double* d, int32_t which,
                                    int32_t k, double* lambda, double* v, int32_t* steps,

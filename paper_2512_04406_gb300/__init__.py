@@ -237,8 +237,17 @@ def manidsdp_lanczos_dense_noalloc(X, d=None, which: int = EIG_MIN, k: int = 0, 
                                    stream: int | None = None):
     """Extreme eigenpair of X - Diag(d) for a device N x N FP64 matrix X (and an
     optional device N-vector d), computed in the library's static scratch with no
-    device allocation.  Returns (lambda, steps); v (N FP64) receives the vector."""
+    device allocation.  Returns (lambda, steps); v (N FP64) receives the vector.
+
+    The C entry point cannot see array sizes, so the shapes are checked here: X
+    must be N x N, d and v must hold N entries; anything else raises ValueError
+    before the library is called."""
+    if len(X.shape) != 2 or int(X.shape[0]) != int(X.shape[1]):
+        raise ValueError("manidsdp_lanczos_dense_noalloc: X must be a square N x N matrix")
     N = int(X.shape[0])
+    for name, a in (("d", d), ("v", v)):
+        if a is not None and tuple(int(s) for s in a.shape) != (N,):
+            raise ValueError(f"manidsdp_lanczos_dense_noalloc: {name} must have shape ({N},)")
     lam = ctypes.c_double()
     steps = ctypes.c_int32()
     st = _lib.manidsdp_lanczos_dense_noalloc(N, _ptr(X, np.float64), _ptr(d, np.float64), which, k,

@@ -1,12 +1,11 @@
 // Extreme eigenpair of a caller-held dense symmetric matrix without any device
-// allocation: manidsdp_lanczos_dense_noalloc.
+// allocation: manidsdp_lanczos_dense_noalloc.  The paper has no counterpart.
 //
-// The work is the certificate check of Algorithm 1 (steps 7-9): Lanczos with
-// full FP64 reorthogonalisation on X - Diag(d), with the iteration, stopping
-// rules and kernels of manidsdp_lanczos, but on a matrix the caller passes in
-// and with the Krylov basis in one static device array instead of a context's
-// workspace.  Nothing here calls cudaMalloc, cudaFree or a library that
-// allocates, and the host side keeps its tridiagonal data in fixed arrays.
+// It runs Lanczos with full FP64 reorthogonalisation on X - Diag(d), with the
+// iteration, stopping rules and kernels of manidsdp_lanczos, but on a matrix the
+// caller passes in and with the Krylov basis in one static device array instead
+// of a context's workspace.  Nothing here calls cudaMalloc, cudaFree or a library
+// that allocates, and the host side keeps its tridiagonal data in fixed arrays.
 //
 // Scratch state: nothing in the array has to be zero at entry.  Every region
 // is written before it is read; the zero diagonal used when d is NULL and the
@@ -15,7 +14,6 @@
 // two streams or two host threads) overwrite each other's basis.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -33,24 +31,20 @@ constexpr size_t kNaDoubles = kNaBasis + 3 * size_t(kNaMaxN) + kNaMaxK + 64;
 
 static __device__ __align__(256) double g_na_scratch[kNaDoubles];
 
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mu;
-double* g_na_ptr[kNaMaxDevices] = {};
-
-// Device address of the scratch for the current device; looked up once per
-// device (the lookup loads the library's module on that device).
+// Device address of the scratch in the current device's context.  In host code
+// g_na_scratch names a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress on every call: after a cudaDeviceReset, or when the
+// primary context is destroyed and created again, the module is loaded anew and
+// the array may sit elsewhere, so a cached address could point at freed or
+// foreign memory.  The lookup allocates nothing; the first one on a device loads
+// the library's module there.
 int na_scratch(double** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
     return MANIDSDP_E_CUDA;
-  std::lock_guard<std::mutex> lock(g_na_mu);
-  if (g_na_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr)
-      return MANIDSDP_E_CUDA;
-    g_na_ptr[dev] = static_cast<double*>(p);
   }
-  *out = g_na_ptr[dev];
+  *out = static_cast<double*>(p);
   return MANIDSDP_OK;
 }
 
@@ -243,7 +237,10 @@ int manidsdp_lanczos_dense_noalloc(int32_t N, const double* X, const double* d, 
         const double res_lo = beta * std::fabs(sv[kk - 1]);
         na_tridiag_vec(al, be, kk, thi, sv);
         const double res_hi = beta * std::fabs(sv[kk - 1]);
-        if (res_lo <= 1e-10 * scale && res_hi <= 1e-6 * scale) {
+        // the requested end of the spectrum to 1e-10, the other (a scale) to 1e-6
+        const double tol_lo = which == MANIDSDP_EIG_MIN ? 1e-10 : 1e-6;
+        const double tol_hi = which == MANIDSDP_EIG_MIN ? 1e-6 : 1e-10;
+        if (res_lo <= tol_lo * scale && res_hi <= tol_hi * scale) {
           steps = kk;
           break;
         }

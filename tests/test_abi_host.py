@@ -108,20 +108,39 @@ def test_ucqp_index_map_and_rhs_bit_exact_vs_oracle(q):
     assert np.array_equal(mds.manidsdp_ucqp_rhs(q, Q, c), ucqp.rhs(q, Q, c, classes))
 
 
+def _noalloc_raw(N, which, k):
+    """The C entry point itself with an explicit N and 1-element dummies: the size
+    checks come before any pointer is read."""
+    import ctypes
+    dummy = np.zeros(1)
+    lam = ctypes.c_double()
+    return mds._lib.manidsdp_lanczos_dense_noalloc(
+        N, dummy.ctypes.data_as(ctypes.c_void_p), None, which, k, ctypes.byref(lam), None,
+        None, None)
+
+
 def test_noalloc_lanczos_rejects_sizes_and_arguments_before_touching_the_gpu():
     """The no-alloc certificate check validates its sizes against the static
     scratch (N <= 16384, k <= 256, k N <= 524288) and its arguments before any
     CUDA call, so these return on a machine without a GPU."""
-    with pytest.raises(mds.ManidsdpError) as e:
-        mds.manidsdp_lanczos_dense_noalloc(np.zeros((16385, 1)), None, mds.EIG_MIN, 4)
-    assert e.value.status == mds.E_TOOLARGE
-    with pytest.raises(mds.ManidsdpError) as e:
-        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4096, 1)), None, mds.EIG_MIN, 129)
-    assert e.value.status == mds.E_TOOLARGE
-    with pytest.raises(mds.ManidsdpError) as e:
-        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4, 4)), None, 7, 4)
-    assert e.value.status == mds.E_ARG
+    assert _noalloc_raw(16385, mds.EIG_MIN, 4) == mds.E_TOOLARGE
+    assert _noalloc_raw(4096, mds.EIG_MIN, 129) == mds.E_TOOLARGE
+    assert _noalloc_raw(4, 7, 4) == mds.E_ARG
+    assert _noalloc_raw(0, mds.EIG_MIN, 4) == mds.E_ARG
     assert "scratch" in mds.manidsdp_strerror(mds.E_TOOLARGE)
+
+
+def test_noalloc_wrapper_checks_shapes_before_the_call():
+    """The binding refuses arrays whose shapes disagree with N (the C entry point
+    reads N x N doubles of X and N of d and v whatever was allocated)."""
+    with pytest.raises(ValueError):
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((16385, 1)), None, mds.EIG_MIN, 4)
+    with pytest.raises(ValueError):
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4, 4)), np.zeros(3), mds.EIG_MIN, 4)
+    with pytest.raises(ValueError):
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros((4, 4)), None, mds.EIG_MIN, 4, np.zeros(5))
+    with pytest.raises(ValueError):
+        mds.manidsdp_lanczos_dense_noalloc(np.zeros(16), None, mds.EIG_MIN, 4)
 
 
 @pytest.mark.parametrize("q,t", [(2, 3), (3, 1), (4, 2), (5, 3), (8, 4), (20, 2)])
