@@ -83,7 +83,7 @@ typedef struct {
   double carry_t0;        /* first step of the carried-direction line search; <= 0: sqrt(N) */
   double round_eta;       /* try the rank-one rounding after outer iterations with
                              eta_max <= round_eta (0 disables it) */
-  int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 256 */
+  int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 512 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */
   int32_t precision_mode; /* MANIDSDP_PREC_* */
@@ -115,8 +115,9 @@ typedef struct {
   double lambda_min, lambda_max, sigma;
   /* device time per phase, summed over the solve (params.profile = 1, else 0):
    * Hessian-vector products, subproblem evaluations (y, G, Psi), gradients
-   * (G Y, z, grad), Lanczos runs */
-  double ms_hessvec, ms_eval, ms_grad, ms_lanczos;
+   * (G Y, z, grad), Lanczos runs (wall clock); ms_rank: host wall clock of the
+   * rank update (eigenvalues of Y'Y, always filled) */
+  double ms_hessvec, ms_eval, ms_grad, ms_lanczos, ms_rank;
   double hessvec_p_sum;       /* sum of p over the Hessian-vector products */
   int32_t outer, rtr_iters, hessvecs, p;
   int32_t lanczos_matvecs, status, evals, grads;

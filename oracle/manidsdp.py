@@ -26,6 +26,15 @@ Readings where the paper is silent (each also listed in the design notes):
     renormalised), keeping p >= p_min; then, if lambda_min(X) < -neg_tol * (1 + |lambda_max(X)|),
     delta = min(#such eigenvalues among the delta_max smallest, delta_max) zero
     columns are appended, p <= p_max.
+  * Inexact subproblems (Algorithm 1 asks only for an approximate solve): RTR
+    stops at eps_k or after max_rtr = 15 iterations, tCG after max_tcg = 60
+    Hessian-vector products.  With this budget the sigma rule (5.1) sees the
+    gradient the capped solve leaves and lowers sigma while the subproblems are
+    far from solved; the rank grows by up to delta_max = 16 directions per outer
+    iteration and directions below rank_tol = 1e-6 lambda_max(Y'Y) are dropped.
+    (Solving every subproblem to eps_k, up to 200 RTR iterations, stalled on the
+    q = 80 relaxation with p held at 256: RTR at its cap in every outer
+    iteration.)
   * tCG also stops once ||r_j|| <= tcg_abs * eps_k (tcg_abs = 0.1): the RTR
     asks for ||grad|| <= eps_k, so resolving the model gradient further is wasted.
   * Use of the carried U (step 3, "supplied with"): if the exact curvature
@@ -57,10 +66,10 @@ from .rtr import rtr
 
 DEFAULTS = dict(
     sigma0=1.0, sigma_min=1e-3, sigma_max=1e6, gamma=2.0, kappa1=0.1, kappa2=10.0,
-    p0=2, p_min=2, p_max=256, delta_max=8,
-    max_outer=300, max_rtr=200, max_tcg=500, tol=1e-8,
+    p0=2, p_min=2, p_max=512, delta_max=16,
+    max_outer=300, max_rtr=15, max_tcg=60, tol=1e-8,
     tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1.0, tcg_floor=1e-10, tcg_abs=0.1,
-    rank_tol=1e-10, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0, round_eta=1e-2,
+    rank_tol=1e-6, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0, round_eta=1e-2,
     lanczos_k=300,
 )
 

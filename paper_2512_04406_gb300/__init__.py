@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "eta_p", "eta_d", "eta_g", "value", "pobj", "lambda_min", "lambda_max", "sigma",
-        "ms_hessvec", "ms_eval", "ms_grad", "ms_lanczos", "hessvec_p_sum")] + [
+        "ms_hessvec", "ms_eval", "ms_grad", "ms_lanczos", "ms_rank", "hessvec_p_sum")] + [
         (n, ctypes.c_int32) for n in (
             "outer", "rtr_iters", "hessvecs", "p", "lanczos_matvecs", "status", "evals",
             "grads")]

@@ -15,8 +15,10 @@
 #include <stdexcept>
 
 #include "common.cuh"
+#include "host_linalg.h"
 
 using namespace mds;
+using namespace mds::hostla;
 
 #include <atomic>
 namespace mds {
@@ -27,130 +29,6 @@ void uncount_launches(long long n) { g_launches.fetch_sub(n, std::memory_order_r
 }  // namespace mds
 
 namespace {
-
-struct HostEig {  // eigenpairs of a small symmetric matrix, ascending
-  std::vector<double> w;
-  std::vector<double> V;  // column-major n x n: V[i + n * j] = component i of vector j
-};
-
-// Cyclic Jacobi rotations on a dense symmetric n x n matrix (row-major input).
-HostEig jacobi_eig(const std::vector<double>& A_in, int n) {
-  std::vector<double> A(A_in);
-  std::vector<double> V(size_t(n) * n, 0.0);
-  for (int i = 0; i < n; ++i) V[i + size_t(n) * i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        const double a = A[size_t(i) * n + j];
-        tot += a * a;
-        if (i != j) off += a * a;
-      }
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[size_t(p) * n + q];
-        if (apq == 0.0) continue;
-        const double app = A[size_t(p) * n + p], aqq = A[size_t(q) * n + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          const double akp = A[size_t(k) * n + p], akq = A[size_t(k) * n + q];
-          A[size_t(k) * n + p] = c * akp - s * akq;
-          A[size_t(k) * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          const double apk = A[size_t(p) * n + k], aqk = A[size_t(q) * n + k];
-          A[size_t(p) * n + k] = c * apk - s * aqk;
-          A[size_t(q) * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[k + size_t(n) * p], vkq = V[k + size_t(n) * q];
-          V[k + size_t(n) * p] = c * vkp - s * vkq;
-          V[k + size_t(n) * q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(),
-            [&](int a, int b) { return A[size_t(a) * n + a] < A[size_t(b) * n + b]; });
-  HostEig out;
-  out.w.resize(n);
-  out.V.resize(size_t(n) * n);
-  for (int j = 0; j < n; ++j) {
-    out.w[j] = A[size_t(order[j]) * n + order[j]];
-    for (int i = 0; i < n; ++i) out.V[i + size_t(n) * j] = V[i + size_t(n) * order[j]];
-  }
-  return out;
-}
-
-// ---- symmetric tridiagonal T (diagonal a[0..k-1], off-diagonal b[0..k-2]) ----
-int sturm_below(const std::vector<double>& a, const std::vector<double>& b, int k, double x) {
-  int cnt = 0;
-  double d = 1.0;
-  for (int i = 0; i < k; ++i) {
-    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
-    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
-    if (d == 0.0) d = -1e-300;
-    if (d < 0) ++cnt;
-  }
-  return cnt;
-}
-
-// i-th smallest eigenvalue (0-based) by bisection on Sturm counts.
-double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int k, int i) {
-  double lo = a[0], hi = a[0];
-  for (int j = 0; j < k; ++j) {
-    const double r = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + (j < k - 1 ? std::fabs(b[j]) : 0.0);
-    lo = std::min(lo, a[j] - r);
-    hi = std::max(hi, a[j] + r);
-  }
-  const double scale = std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
-  for (int it = 0; it < 200 && hi - lo > 1e-17 * scale; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_below(a, b, k, mid) > i)
-      hi = mid;
-    else
-      lo = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
-// Eigenvector of T for eigenvalue theta by inverse iteration (LU without pivoting,
-// tiny pivots replaced), orthogonalised against `prev`.
-std::vector<double> tridiag_vec(const std::vector<double>& a, const std::vector<double>& b, int k,
-                                double theta, const std::vector<std::vector<double>>& prev) {
-  double tn = 0.0;
-  for (int j = 0; j < k; ++j) tn = std::max(tn, std::fabs(a[j]) + (j < k - 1 ? std::fabs(b[j]) : 0.0));
-  const double tiny = 1e-14 * (tn + 1e-300);
-  std::vector<double> x(k), u(k), l(k), d(k);
-  for (int j = 0; j < k; ++j) x[j] = 1.0 + 0.01 * ((j * 7919) % 101);
-  for (int it = 0; it < 4; ++it) {
-    // factor T - theta I = L U with U bidiagonal (d on diagonal, b above)
-    d[0] = a[0] - theta;
-    if (std::fabs(d[0]) < tiny) d[0] = tiny;
-    for (int j = 1; j < k; ++j) {
-      l[j] = b[j - 1] / d[j - 1];
-      d[j] = (a[j] - theta) - l[j] * b[j - 1];
-      if (std::fabs(d[j]) < tiny) d[j] = tiny;
-    }
-    for (int j = 1; j < k; ++j) x[j] -= l[j] * x[j - 1];
-    x[k - 1] /= d[k - 1];
-    for (int j = k - 2; j >= 0; --j) x[j] = (x[j] - b[j] * x[j + 1]) / d[j];
-    for (const auto& pv : prev) {
-      double dp = 0.0;
-      for (int j = 0; j < k; ++j) dp += pv[j] * x[j];
-      for (int j = 0; j < k; ++j) x[j] -= dp * pv[j];
-    }
-    double nrm = 0.0;
-    for (int j = 0; j < k; ++j) nrm += x[j] * x[j];
-    nrm = std::sqrt(nrm);
-    for (int j = 0; j < k; ++j) x[j] /= nrm;
-  }
-  return x;
-}
 
 // splitmix64 (Steele, Lea, Flood 2014): the start vector of Lanczos.
 uint64_t splitmix64(uint64_t x) {
@@ -223,7 +101,7 @@ struct manidsdp_ctx {
   // counters and phase timers
   int hessvecs = 0, rtr_iters = 0, lanczos_mv = 0, evals = 0, grads = 0;
   double hv_psum = 0.0;
-  double ms_hv = 0.0, ms_eval = 0.0, ms_grad = 0.0, ms_lz = 0.0;
+  double ms_hv = 0.0, ms_eval = 0.0, ms_grad = 0.0, ms_lz = 0.0, ms_rank = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-stage Hess-vec timing (params.profile == 2, host-driven path)
   cudaEvent_t sev[8] = {};
@@ -292,8 +170,12 @@ float* g32(manidsdp_ctx* c) { return mixed(c) ? c->Gh : c->Gf; }
 
 // T = G U - sigma A*(w) Y of the FP32 Hessian-vector product as split-K partial
 // products in c->gws (tensor cores or FP32 FMA); returns the number of splits.
+// The tensor-core kernel holds at most 256 accumulator columns; wider factors
+// take the FMA kernel.
+bool use_tc(const manidsdp_ctx* c, int p) { return c->prm.tensor_cores && p <= 256; }
+
 int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
-  if (c->prm.tensor_cores)
+  if (use_tc(c, p))
     return launch_tc_gather_gemm_partials(c->N, p, g32(c), c->Upf, c->idx, c->wf,
                                           float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
                                           c->tc_err, s);
@@ -304,7 +186,7 @@ int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
 void drop_graphs(manidsdp_ctx* c);
 
 int gather_gemm32_splits(manidsdp_ctx* c, int p) {
-  return c->prm.tensor_cores ? tc_gather_gemm_splits(c->N, p, c->gws_bytes)
+  return use_tc(c, p) ? tc_gather_gemm_splits(c->N, p, c->gws_bytes)
                              : gemm32_splits(c->N, p, c->gws_bytes);
 }
 
@@ -576,7 +458,7 @@ void default_params(manidsdp_params* p) {
   p->tol_grad_min = 1e-11;
   p->tol_grad_max = 1e-2;
   p->tol_grad_factor = 1.0;
-  p->rank_tol = 1e-10;
+  p->rank_tol = 1e-6;
   p->neg_tol = 1e-10;
   p->tcg_floor = 1e-10;
   p->tcg_abs = 0.1;
@@ -585,11 +467,11 @@ void default_params(manidsdp_params* p) {
   p->warm_start = 0;
   p->p0 = 2;
   p->p_min = 2;
-  p->p_max = 256;
-  p->delta_max = 8;
+  p->p_max = 512;
+  p->delta_max = 16;
   p->max_outer = 300;
-  p->max_rtr = 200;
-  p->max_tcg = 500;
+  p->max_rtr = 15;
+  p->max_tcg = 60;
   p->carry_halvings = 30;
   p->lanczos_k = 300;
   p->precision_mode = MANIDSDP_PREC_FP64;
@@ -602,7 +484,7 @@ void default_params(manidsdp_params* p) {
 // Ranges of the parameters (the switches are 0 or 1).
 bool params_ok(const manidsdp_params& p) {
   auto flag = [](int32_t v) { return v == 0 || v == 1; };
-  return p.p_max >= 1 && p.p_max <= 256 && p.p0 >= 1 && p.p0 <= p.p_max && p.p_min >= 1 &&
+  return p.p_max >= 1 && p.p_max <= kMaxP && p.p0 >= 1 && p.p0 <= p.p_max && p.p_min >= 1 &&
          p.delta_max >= 0 && p.lanczos_k >= 1 && p.max_outer >= 0 && p.max_rtr >= 0 &&
          p.max_tcg >= 1 && p.carry_halvings >= 0 &&
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
@@ -1239,8 +1121,9 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
   int gst = guard([&]() -> int {
     const int N = c->N;
     const manidsdp_params& P = c->prm;
+    const auto t_solve0 = std::chrono::steady_clock::now();
     c->hessvecs = c->rtr_iters = c->lanczos_mv = c->evals = c->grads = 0;
-    c->hv_psum = c->ms_hv = c->ms_eval = c->ms_grad = c->ms_lz = 0.0;
+    c->hv_psum = c->ms_hv = c->ms_eval = c->ms_grad = c->ms_lz = c->ms_rank = 0.0;
     const bool resume = P.warm_start && c->resume_valid;
     int p = p0;
     double rscale = -1.0;
@@ -1335,9 +1218,11 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       if (P.verbose)
         std::fprintf(stderr,
                      "[manidsdp] k=%d p=%d sigma=%.3g rtr=%d(rej %d, bnd %d, D %.2e) gnorm=%.3e "
-                     "tol=%.2e eta=(%.2e %.2e %.2e) lmin=%.3e V=%.12f hv=%d lz=%d\n",
+                     "tol=%.2e eta=(%.2e %.2e %.2e) lmin=%.3e V=%.12f hv=%d lz=%d t=%.3fs\n",
                      k, p, sigma, ro.iters, ro.rejected, ro.boundary, ro.delta_end, ro.gnorm, tol_k,
-                     rep.eta_p, rep.eta_d, rep.eta_g, lo.lo[0], by, c->hessvecs, lo.steps);
+                     rep.eta_p, rep.eta_d, rep.eta_g, lo.lo[0], by, c->hessvecs, lo.steps,
+                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t_solve0)
+                         .count());
       if (!std::isfinite(eta)) {
         status = MANIDSDP_E_NONFINITE;
         break;
@@ -1352,12 +1237,14 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
         std::vector<double> A(size_t(p) * p);
         MDS_CUDA(cudaMemcpyAsync(A.data(), c->M2, A.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
         sync(c);
-        HostEig e = jacobi_eig(A, p);
+        const auto th0 = std::chrono::steady_clock::now();
+        const SymTridiag T = sym_tridiag(A, p);
+        const double wmax = tridiag_eig(T.d, T.e, p, p - 1);
         // rank-one rounding: Yr = sign(Y w), w the top eigenvector of Y'Y; accept when
         // Yr Yr' is consistent with the classes (R = 0) and its certificate is PSD
         if (eta <= P.round_eta) {
-          std::vector<double> wtop(p);
-          for (int i = 0; i < p; ++i) wtop[i] = e.V[i + size_t(p) * (p - 1)];
+          std::vector<double> wtop = tridiag_vec(T.d, T.e, p, wmax, {});
+          tridiag_backtransform(T, wtop);
           MDS_CUDA(cudaMemcpyAsync(c->M1, wtop.data(), p * sizeof(double), cudaMemcpyHostToDevice, c->s));
           launch_gemm<double>(N, 1, p, c->Y, p, c->M1, 1, c->GY, 1, 1.0, 0.0, nullptr, nullptr,
                               0.0, nullptr, c->gws, c->gws_bytes, c->s);
@@ -1398,21 +1285,26 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
             }
           }
         }
-        const double wmax = e.w[p - 1];
-        std::vector<int> keep;
-        for (int i = 0; i < p; ++i)
-          if (e.w[i] > P.rank_tol * wmax || i >= p - P.p_min) keep.push_back(i);
-        const int r = int(keep.size());
+        // keep the eigendirections of Y'Y above rank_tol * lambda_max, at least p_min
+        const int nlow = sturm_below(T.d, T.e, p, P.rank_tol * wmax);
+        const int r = std::max(p - nlow, std::min(P.p_min, p));
         if (r < p) {
-          std::vector<double> W(size_t(p) * r);  // row-major p x r
-          for (int i = 0; i < p; ++i)
-            for (int j = 0; j < r; ++j) W[size_t(i) * r + j] = e.V[i + size_t(p) * keep[j]];
+          std::vector<std::vector<double>> vecs;  // eigenvectors of T, descending
+          for (int i = p - 1; i >= p - r; --i)
+            vecs.push_back(tridiag_vec(T.d, T.e, p, tridiag_eig(T.d, T.e, p, i), vecs));
+          std::vector<double> W(size_t(p) * r);  // row-major p x r, columns ascending
+          for (int j = 0; j < r; ++j) {
+            std::vector<double> x = vecs[r - 1 - j];
+            tridiag_backtransform(T, x);
+            for (int i = 0; i < p; ++i) W[size_t(i) * r + j] = x[i];
+          }
           MDS_CUDA(cudaMemcpyAsync(c->M1, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
           launch_gemm<double>(N, r, p, c->Y, p, c->M1, r, c->tmp, r, 1.0, 0.0, nullptr, nullptr,
                               0.0, nullptr, c->gws, c->gws_bytes, c->s);
           launch_retract(N, r, c->tmp, c->tmp, 0.0, c->Y, c->s);
           p = r;
         }
+        c->ms_rank += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
       }
       // step 11: sigma rule (5.1)
       const double lhs = rnorm / (1.0 + c->normb);
@@ -1454,6 +1346,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     rep.ms_eval = c->ms_eval;
     rep.ms_grad = c->ms_grad;
     rep.ms_lanczos = c->ms_lz;
+    rep.ms_rank = c->ms_rank;
     rep.status = status;
     if (Y_out) MDS_CUDA(cudaMemcpyAsync(Y_out, c->Y, size_t(N) * rep.p * sizeof(double), cudaMemcpyDefault, c->s));
     if (p_out) *p_out = rep.p;

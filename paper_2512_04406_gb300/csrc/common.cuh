@@ -14,6 +14,7 @@ namespace mds {
 // Entries of the per-class inverse map pack (row, col) as (row << 16) | col,
 // so N must stay below 65536.
 constexpr int kMaxN = 65535;
+constexpr int kMaxP = 512;  // widest factor: row-local kernels hold 16 columns per lane
 // A class's entries are processed in pieces of at most this many entries.
 constexpr int kPieceLen = 32;
 // Threads of the reduction kernels; the partial-sum buffers hold kRedBlocks values.

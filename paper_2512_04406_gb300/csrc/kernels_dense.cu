@@ -422,7 +422,7 @@ __global__ void hv_epilogue_kernel(int N, int p, int splits, const T* __restrict
   const size_t np = size_t(N) * p;
   const T* M1 = M;
   const T* M2 = M + size_t(p) * p;
-  constexpr int MAXC = 8;  // columns per lane held in registers (p <= 256)
+  constexpr int MAXC = 16;  // columns per lane held in registers (p <= 512)
   double ht[MAXC];
   double d = 0.0;
 #pragma unroll

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) tcg_epilogue_kernel(
     const size_t np = size_t(N) * p;
     const T* M1 = M;
     const T* M2 = M + size_t(p) * p;
-    constexpr int MAXC = 8;
+    constexpr int MAXC = 16;  // columns per lane held in registers (p <= 512)
     double ht[MAXC];
     double d = 0.0;
 #pragma unroll

@@ -35,8 +35,13 @@ def test_library_exports_every_declared_symbol():
 def test_default_params_match_documented_readings():
     p = mds.manidsdp_default_params()
     assert (p.sigma0, p.sigma_min, p.sigma_max, p.gamma, p.kappa1, p.kappa2) == (1.0, 1e-3, 1e6, 2.0, 0.1, 10.0)
-    assert p.tol == 1e-8 and p.p0 == 2 and p.p_min == 2 and p.delta_max == 8
+    assert p.tol == 1e-8 and p.p0 == 2 and p.p_min == 2 and p.delta_max == 16
     assert mds.manidsdp_strerror(-1) == "invalid argument"
+    # the library and the oracle implement the same readings with the same constants
+    from oracle.manidsdp import DEFAULTS
+    for k, v in DEFAULTS.items():
+        if hasattr(p, k):
+            assert getattr(p, k) == v, k
 
 
 @pytest.mark.parametrize("q,order", [(1, 2), (2, 2), (3, 2), (5, 2), (9, 2), (20, 2), (4, 1), (17, 1)])
@@ -85,7 +90,7 @@ def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
 
 @pytest.mark.parametrize("field,value", [("tensor_cores", 2), ("precision_mode", 5),
                                          ("tcg_device", -1), ("warm_start", 3), ("gamma", 1.0),
-                                         ("p_max", 257), ("max_tcg", 0), ("sigma0", 0.0)])
+                                         ("p_max", 513), ("max_tcg", 0), ("sigma0", 0.0)])
 def test_setup_rejects_out_of_range_params_before_touching_the_gpu(field, value):
     N, m, idx = mds.manidsdp_bqp_index_map(3, 2)
     prm = mds.manidsdp_default_params()
