@@ -5,7 +5,7 @@
 // sizes when the loop is host-driven, trust-region ratio, sigma rule, rank
 // update); every vector and matrix operation runs in the kernels: kernels_seg.cu
 // and kernels_dense.cu (FP64 form), kernels_df64.cu (df64 evaluation),
-// kernels_sddmm.cu, kernels_gemm32.cu and kernels_tc.cu (FP32 Hessian-vector
+// kernels_sddmm.cu, kernels_gemm32.cu and kernels_tcx.cu (FP32 Hessian-vector
 // product), kernels_tcg.cu (device-driven truncated CG).
 #include <algorithm>
 #include <chrono>
@@ -96,6 +96,13 @@ struct manidsdp_ctx {
   double resume_rscale = -1.0;
   int resume_outer = 0;
   int* tc_err = nullptr;  // set by a tensor-core kernel whose device-side wait timed out
+  // TMA tensor-core engine of the FP32 Hess-vec: its operands as TF32 pairs
+  float *Ghi = nullptr, *Glo = nullptr, *QWhi = nullptr, *QWlo = nullptr;  // N x ldg
+  float *Yxh = nullptr, *Yxl = nullptr, *Uxh = nullptr, *Uxl = nullptr;    // N x ld(p)
+  float *YTh = nullptr, *YTl = nullptr, *UTh = nullptr, *UTl = nullptr;    // p x ldg
+  float* Wfull = nullptr;  // W = Y Up' + Up Y' at every entry (N x ldg)
+  int2* tiles = nullptr;  // upper-triangle 128 x 128 tile pairs of the SDDMM
+  int ntiles = 0;
   bool resume_have_U = false;  // the last iteration augmented Y = [Y, 0] and set U = [0, V]
   int resume_U_cols = 0;
   // counters and phase timers
@@ -170,15 +177,73 @@ float* g32(manidsdp_ctx* c) { return mixed(c) ? c->Gh : c->Gf; }
 
 // T = G U - sigma A*(w) Y of the FP32 Hessian-vector product as split-K partial
 // products in c->gws (tensor cores or FP32 FMA); returns the number of splits.
-// The tensor-core kernel holds at most 256 accumulator columns; wider factors
-// take the FMA kernel.
-bool use_tc(const manidsdp_ctx* c, int p) { return c->prm.tensor_cores && p <= 256; }
+// The tensor-core engine of the FP32 Hess-vec (kernels_tcx.cu): TMA-fed tcgen05
+// SDDMM, Gram products and gather GEMM.
+bool use_tcx(const manidsdp_ctx* c) { return c->prm.tensor_cores == 1; }
 
+// Buffers of the tensor-core engine, allocated on first use (outside any capture).
+void ensure_tcx(manidsdp_ctx* c) {
+  if (c->Ghi != nullptr) return;
+  const int N = c->N, ldg = tcx_ld(N), ldp = tcx_ld(c->pcap);
+  const size_t nn = size_t(N) * ldg, np = size_t(N) * ldp, pn = size_t(c->pcap) * ldg;
+  c->Ghi = dalloc<float>(c, nn);
+  c->Glo = dalloc<float>(c, nn);
+  c->QWhi = dalloc<float>(c, nn);
+  c->QWlo = dalloc<float>(c, nn);
+  c->Wfull = dalloc<float>(c, nn);
+  float** rows[] = {&c->Yxh, &c->Yxl, &c->Uxh, &c->Uxl};
+  for (float** q : rows) *q = dalloc<float>(c, np);
+  float** cols[] = {&c->YTh, &c->YTl, &c->UTh, &c->UTl};
+  for (float** q : cols) *q = dalloc<float>(c, pn);
+  const std::vector<int2> t = tcx_upper_tiles(N);
+  c->ntiles = int(t.size());
+  c->tiles = dalloc<int2>(c, t.size());
+  MDS_CUDA(cudaMemcpyAsync(c->tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, c->s));
+}
+
+// The current point for the tensor-core engine: G (from its FP32 copy) and Y as
+// TF32 pairs, Y also transposed.
+void tcx_point(manidsdp_ctx* c, const double* Y, int p, cudaStream_t s) {
+  ensure_tcx(c);
+  const int N = c->N, ldg = tcx_ld(N), ldp = tcx_ld(p);
+  launch_tcx_split_matrix(N, g32(c), nullptr, nullptr, 0.f, c->Ghi, c->Glo, ldg, s);
+  launch_tcx_split_rows(N, p, Y, c->Yxh, c->Yxl, ldp, c->YTh, c->YTl, ldg, s);
+}
+
+// Tensor-core Hess-vec body after the prologue (Up in FP64): Up as TF32 pairs, the
+// SDDMM (class sums w and the full W), sigma Q(W) = sigma (W - A*(w)) as pairs and
+// the gather GEMM G Up + sigma Q(W) Y.  Returns the number of split-K slices minus
+// one: the epilogue adds the last slice where the FMA engine has its separate
+// Y(U'Y) + U(Y'Y) slice.
+int hessvec_tcx(manidsdp_ctx* c, int p, cudaStream_t s, const std::function<void(int)>& mark) {
+  const int N = c->N, ldg = tcx_ld(N), ldp = tcx_ld(p);
+  launch_tcx_split_rows(N, p, c->Up, c->Uxh, c->Uxl, ldp, c->UTh, c->UTl, ldg, s);
+  if (mark) mark(1);
+  launch_tcx_sddmm(N, p, c->Yxh, c->Yxl, c->Uxh, c->Uxl, ldp, c->slot, c->perm, c->Wfull, ldg,
+                   c->tiles, c->ntiles, c->tc_err, s);
+  launch_piece_sums(c->cm, c->perm, c->mult, reinterpret_cast<float*>(c->piece_buf), c->wf, s);
+  if (mark) mark(2);
+  launch_tcx_split_matrix(N, c->Wfull, c->idx, c->wf, float(c->sigma), c->QWhi, c->QWlo, ldg, s);
+  const int S = launch_tcx_gather(N, p, c->Ghi, c->Glo, c->QWhi, c->QWlo, ldg, c->UTh, c->UTl,
+                                  c->YTh, c->YTl, ldg, static_cast<float*>(c->gws), c->gws_bytes,
+                                  c->tc_err, s);
+  if (mark) {
+    mark(3);
+    mark(4);
+  }
+  return S - 1;
+}
+
+// w = A(Y Up' + Up Y') / mult in FP32 on the FMA engine (tiled SDDMM into the
+// class-ordered buffer, per-piece sums).
+void class_sums32(manidsdp_ctx* c, int p, cudaStream_t s) {
+  float* pbf = reinterpret_cast<float*>(c->piece_buf);
+  launch_sddmm_means(c->cm, c->N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
+}
+
+// T = G U - sigma A*(w) Y of the FP32 Hessian-vector product on the FMA engine as
+// split-K partial products in c->gws; returns the number of splits.
 int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
-  if (use_tc(c, p))
-    return launch_tc_gather_gemm_partials(c->N, p, g32(c), c->Upf, c->idx, c->wf,
-                                          float(-c->sigma), c->Yf, c->gws, c->gws_bytes,
-                                          c->tc_err, s);
   return launch_gemm32_partials(c->N, p, g32(c), c->Upf, c->idx, c->wf, float(-c->sigma), c->Yf,
                                 c->gws, c->gws_bytes, s);
 }
@@ -186,15 +251,16 @@ int gather_gemm32(manidsdp_ctx* c, int p, cudaStream_t s) {
 void drop_graphs(manidsdp_ctx* c);
 
 int gather_gemm32_splits(manidsdp_ctx* c, int p) {
-  return use_tc(c, p) ? tc_gather_gemm_splits(c->N, p, c->gws_bytes)
-                             : gemm32_splits(c->N, p, c->gws_bytes);
+  if (use_tcx(c)) return tcx_gather_splits(c->N) - 1;
+  return gemm32_splits(c->N, p, c->gws_bytes);
 }
 
 // The FP32 Hess-vec after its prologue (Upf, Yf, Y'Y in place) up to the
-// split-K partials in c->gws: class sums and gather GEMM on s; U'Y and the
-// Y(U'Y) + U(Y'Y) slice on the side stream when fork is set (joined before
-// return), else on s after the GEMM.  Returns the number of GEMM splits.
+// split-K partials in c->gws.  FMA engine: class sums and gather GEMM on s; U'Y
+// and the Y(U'Y) + U(Y'Y) slice on the side stream when fork is set (joined
+// before return), else on s after the GEMM.  Returns the number of GEMM splits.
 int hessvec32_body(manidsdp_ctx* c, int p, cudaStream_t s, bool fork) {
+  if (use_tcx(c)) return hessvec_tcx(c, p, s, nullptr);
   const int N = c->N;
   const int splits = gather_gemm32_splits(c, p);
   float* ym_out = static_cast<float*>(c->gws) + size_t(splits) * N * p;
@@ -205,8 +271,7 @@ int hessvec32_body(manidsdp_ctx* c, int p, cudaStream_t s, bool fork) {
     launch_ym32(N, p, c->Yf, c->Upf, c->M1f, float(c->sigma), ym_out, c->s2);
     MDS_CUDA(cudaEventRecord(c->ev_join, c->s2));
   }
-  float* pbf = reinterpret_cast<float*>(c->piece_buf);
-  launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
+  class_sums32(c, p, s);
   if (gather_gemm32(c, p, s) != splits) throw DeviceError{cudaErrorInvalidValue};
   if (fork) {
     MDS_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -302,14 +367,17 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
     const bool fresh = !c->yf_valid;
     launch_hv_prep<float>(N, p, Y, U, c->Up, c->Upf, c->Yf, fresh, c->s);
     c->yf_valid = true;
-    if (fresh)  // Y'Y depends on Y only: second p x p slot of M1f
+    if (fresh) {  // Y'Y depends on Y only: second p x p slot of M1f
       launch_gram2<float>(N, p, c->Yf, nullptr, c->Yf, c->M1f + size_t(p) * p, c->gws2,
                           c->gws2_bytes, c->s);
-    mark(1);
+      if (use_tcx(c)) tcx_point(c, Y, p, c->s);
+    }
+    if (!(stages && use_tcx(c))) mark(1);
     int splits;
-    if (stages) {  // serial, with the stage events between the steps
-      float* pbf = reinterpret_cast<float*>(c->piece_buf);
-      launch_sddmm_means(c->cm, N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, c->s);
+    if (stages && use_tcx(c)) {  // Gram products in stage 0, the Q(W) Y term in stage 2
+      splits = hessvec_tcx(c, p, c->s, mark);
+    } else if (stages) {  // serial, with the stage events between the steps
+      class_sums32(c, p, c->s);
       mark(2);
       splits = gather_gemm32(c, p, c->s);
       mark(3);
@@ -660,7 +728,6 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     MDS_CUDA(cudaMemcpyAsync(c->idx, idx, NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
     c->tc_err = dalloc<int>(c, 1);
     MDS_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->s));
-    tc_gather_gemm_prepare();
     c->mult = dalloc<double>(c, m);
     MDS_CUDA(cudaMemcpyAsync(c->mult, mult.data(), m * sizeof(double), cudaMemcpyHostToDevice, c->s));
     c->b = dalloc<double>(c, m);
@@ -739,7 +806,8 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->part = dalloc<double>(c, gpass_partials(N));
     c->out2 = dalloc<double>(c, 2);
     c->dpart = dalloc<double>(c, 3 * kRedBlocks + 3);
-    c->gws_bytes = (np + size_t(2) * 304 * 4096) * sizeof(double);
+    c->gws_bytes = std::max((np + size_t(2) * 304 * 4096) * sizeof(double),
+                            size_t(tcx_gather_splits(N) + 1) * np * sizeof(float));
     c->gws = dalloc<double>(c, c->gws_bytes / sizeof(double));
     c->gws2_bytes = size_t(1) << 21;
     c->gws2 = dalloc<double>(c, c->gws2_bytes / sizeof(double));
@@ -1020,6 +1088,7 @@ TcgOut tcg_device(manidsdp_ctx* c, int p, double Delta, double tol_grad) {
     launch_to_float(n, c->Y, c->Yf, c->s);
     launch_gram2<float>(N, p, c->Yf, nullptr, c->Yf, c->M1f + size_t(p) * p, c->gws2,
                         c->gws2_bytes, c->s);
+    if (use_tcx(c)) tcx_point(c, c->Y, p, c->s);
     c->yf_valid = true;
   }
   MDS_CUDA(cudaMemsetAsync(c->eta, 0, n * sizeof(double), c->s));

@@ -110,6 +110,35 @@ void launch_spass_df(const ClassMap& cm, int N, int p, const float* Yh, const fl
 void launch_gemm_df(int N, int ncol, const float* Gh, const float* Gl, const float* Yh,
                     const float* Yl, double* out, void* ws, size_t ws_bytes, cudaStream_t s);
 
+// ---- TMA-fed tensor-core engine of the FP32 Hess-vec (kernels_tcx.cu) ------
+// Operands are FP32 values held as TF32 pairs (hi, lo) in row-major arrays whose
+// leading dimensions are multiples of 4 (tcx_ld).
+int tcx_ld(int n);
+// X (N x p FP64) as TF32 pairs: rows (leading dimension ld) and, when hiT is not
+// null, transposed (p x N, leading dimension ldt).
+void launch_tcx_split_rows(int N, int p, const double* X, float* hi, float* lo, int ld, float* hiT,
+                           float* loT, int ldt, cudaStream_t s);
+// G (N x N FP32, leading dimension N) or, when idx is given, the projector residual
+// gscale * (G - w[idx]) with G the full W (leading dimension ld), as TF32 pairs.
+void launch_tcx_split_matrix(int N, const float* G, const int32_t* idx, const float* w,
+                             float gscale, float* hi, float* lo, int ld, cudaStream_t s);
+// Split-K partials [splits][N][p] of T = G Up + QW Y (QW = sigma Q(W)) from TF32 pairs;
+// returns the number of splits, tcx_gather_splits(N).
+int tcx_gather_splits(int N);
+int launch_tcx_gather(int N, int p, const float* Ghi, const float* Glo, const float* QWhi,
+                      const float* QWlo, int ldg, const float* UThi, const float* UTlo,
+                      const float* YThi, const float* YTlo, int ldt, float* part, size_t ws_bytes,
+                      int* err, cudaStream_t s);
+// W = Y U' + U Y' on the upper-triangle tiles: entry (r <= c) weighted 2 off the
+// diagonal written to perm[slot[r N + c]], and every entry of W into wfull (ldw).
+void launch_tcx_sddmm(int N, int p, const float* Yhi, const float* Ylo, const float* Uhi,
+                      const float* Ulo, int ld, const int32_t* slot, float* perm, float* wfull,
+                      int ldw, const int2* tiles, int ntiles, int* err, cudaStream_t s);
+std::vector<int2> tcx_upper_tiles(int N);
+// Per-piece sums of the class-ordered buffer into out[a] / mult[a] (kernels_sddmm.cu).
+void launch_piece_sums(const ClassMap& cm, const float* perm, const double* mult,
+                       float* piece_buf, float* out, cudaStream_t s);
+
 // Tiled SDDMM class sums (kernels_sddmm.cu): out[a] = A(Y U' + U Y')_a / mult[a] in FP32.
 void launch_sddmm_means(const ClassMap& cm, int N, int p, const float* Y, const float* U,
                         const int32_t* slot, float* perm, const double* mult, float* piece_buf,
@@ -121,23 +150,13 @@ int launch_gemm32_partials(int N, int ncol, const float* G, const float* U, cons
                            const float* w, float gscale, const float* Y, void* ws, size_t ws_bytes,
                            cudaStream_t s);
 
+// Number of split-K partial products launch_gemm32_partials writes for these sizes;
+// the YM slice goes right after them.
+int gemm32_splits(int N, int ncol, size_t ws_bytes);
+
 // out = scale * (Y M1 + Up M2), M = [M1; M2] (2p x p), FP32 (kernels_gemm32.cu)
 void launch_ym32(int N, int p, const float* Y, const float* Up, const float* M, float scale,
                  float* out, cudaStream_t s);
-
-// The same partial products on the tensor cores (tcgen05 kind::tf32, two-term TF32
-// split), kernels_tc.cu.  ncol <= 256.  *err is set to 1 when a device-side wait
-// of a CTA hit its limit.  tc_gather_gemm_prepare raises the kernel's dynamic
-// shared-memory limit; call it once per device before the first launch.
-void tc_gather_gemm_prepare();
-// Number of split-K partial products the launchers below (and launch_gemm32_partials)
-// will write for these sizes; the YM slice goes right after them.
-int tc_gather_gemm_splits(int N, int ncol, size_t ws_bytes);
-int gemm32_splits(int N, int ncol, size_t ws_bytes);
-int launch_tc_gather_gemm_partials(int N, int ncol, const float* G, const float* U,
-                                   const int32_t* idx, const float* w, float gscale,
-                                   const float* Y, void* ws, size_t ws_bytes, int* err,
-                                   cudaStream_t s);
 
 // ---- device-driven tCG (kernels_tcg.cu) ----
 size_t tcg_state_bytes();

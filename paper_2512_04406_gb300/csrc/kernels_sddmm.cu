@@ -131,6 +131,20 @@ __global__ void piece_finalize_kernel(int n_multi, const int32_t* __restrict__ m
   out[cls] = float(s / mult[cls]);
 }
 
+void launch_piece_sums(const ClassMap& cm, const float* perm, const double* mult,
+                       float* piece_buf, float* out, cudaStream_t s) {
+  count_launches(1);
+  piece_sum_kernel<<<(cm.n_pieces + 255) / 256, 256, 0, s>>>(cm.n_pieces, cm.piece_start,
+                                                            cm.piece_class, perm, mult, piece_buf,
+                                                            out);
+  if (cm.n_multi > 0) {
+    count_launches(1);
+    piece_finalize_kernel<<<(cm.n_multi + 255) / 256, 256, 0, s>>>(
+        cm.n_multi, cm.multi_class, cm.multi_range, piece_buf, mult, out);
+  }
+  MDS_CUDA(cudaGetLastError());
+}
+
 void launch_sddmm_means(const ClassMap& cm, int N, int p, const float* Y, const float* U,
                         const int32_t* slot, float* perm, const double* mult, float* piece_buf,
                         float* out, cudaStream_t s) {
