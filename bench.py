@@ -6,27 +6,32 @@ min x'Qx + c'x over x in {-1,1}^80 (Section 6.1): moment matrix 3241 x 3241,
 1,666,981 classes (monomials of degree <= 4), Q and c iid N(0,1) from seed 0,
 p_0 = ceil(ln m) = 15 (Section 6.1 sets p_0 = ceil(log m)).
 
-A step is one pass of the whole hot path: one ALM outer iteration of Algorithm 1
-(the RTR solve of the subproblem with its tCG Hessian-vector products, the
-multiplier update, the Lanczos certificate check, the rank and sigma updates), in
-the mixed-precision form (FP32 Hessian-vector products, df64 cost and gradient,
-FP64 multiplier, KKT residuals and Lanczos).  The W warm-up steps are the first W
-outer iterations of a fresh solve from the seeded start; the K timed steps are
-the next K outer iterations of the same solve (warm start: factor, multiplier
-and penalty carried over).  Inputs sit in HBM before the timed region; the
-working set (index map 42 MB, N x N FP64 multiplier and G 168 MB) exceeds the
-129 MB L2, so no flush is needed between steps.  Beside the headline the line
-reports a full solve to eta_max <= 1e-8 of the q = 60 instance (N = 1831) and
-the same q = 40 instance solved by the mixed and by the plain FP64 form.
+A step is one complete solve of Algorithm 1 from the seeded start to
+eta_max <= 1e-8 (every ALM outer iteration: the RTR solve of the subproblem with
+its tCG Hessian-vector products, the multiplier update, the Lanczos certificate
+check, the rank and sigma updates, the rank-one rounding), in the
+mixed-precision form (tensor-core FP32 Hessian-vector products, df64 cost and
+gradient, FP64 multiplier, KKT residuals and Lanczos).  Every step restarts from
+the same seeded factor with a zero multiplier, so all steps do the same work.
+The inputs (index map, b) sit in HBM before the timed region; the working set
+(index map 42 MB, N x N FP64 multiplier and G 84 MB each, the tensor-core
+operand pairs 168 MB) exceeds the 129 MB L2, so no flush is needed between
+steps.  value = CUDA-event time of the K timed solves / K, in s per solve.
 
-Under torchrun (N > 1) each rank runs its own replica (the single-instance path
-has no exchange step); value = max-over-ranks time / (K x ranks), the job's time
-per outer iteration.
+Beside the headline the line reports the same comparison for the plain FP64
+GPU form (`mixed_vs_fp64`, at --fp64-q, default 40; the FP64 form at q = 80
+takes minutes), the Hess-vec's rate against the tensor pipe (`roofline`), an
+end-to-end solve through the C ABI from pinned host buffers (`e2e`) and the FP64
+oracle timed on the host cores (`cpu_baseline`).
 
-`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (its Hessian-vector product, cost-plus-gradient
-evaluation and certificate matvec) and scales it to one outer iteration by the
-operation counts of an outer iteration (see the JSON's cpu_baseline.sample).
+Under torchrun (N > 1) each rank solves its own replica (the single-instance
+path has no exchange step); value = max-over-ranks time / (K x ranks).
+
+`--impl reference` times the FP64 CPU oracle, as it stands, on the host cores:
+each step executes a bounded sample of the same workload (Hessian-vector
+products, cost-plus-gradient evaluations and certificate matvecs at the factor
+width the GPU solve averages) and scales it to one solve by the operation
+counts of the GPU solve (see the JSON's cpu_baseline.sample).
 """
 from __future__ import annotations
 
@@ -47,47 +52,39 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "solve time to KKT≤1e-8 (mixed vs FP64 GPU); Hess-vec GB/s or TC % of roofline"
-UNIT = "s/ALM-outer-iteration"
+UNIT = "s/solve"
 
-# Operation counts of one outer iteration of this workload (means over the timed
-# steps of a GPU run), used to scale the sampled oracle timings to one outer
-# iteration when no GPU run precedes them.  The GPU arm uses the counts of its
-# own timed steps.
-DEFAULT_COUNTS = dict(hessvecs=6622, evals=164, grads=170, lanczos_matvecs=115, p=49)
+# Operation counts of one solve of this workload in the mixed form with the
+# tensor-core engine (GB300 run of this bench), used to scale the oracle's
+# sampled timings to one solve when no GPU run precedes them (the reference arm).
+# The GPU arm uses the counts of its own timed solves.
+DEFAULT_COUNTS = dict(hessvecs=23137, evals=1140, grads=591, lanczos_matvecs=10290, p=341,
+                      outer=40)
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one
-# Hess-vec) from one ncu capture at q = 80 and the p of the timed steps, per gather-GEMM
-# engine of the mixed form.  "current" is False when kernels of the Hess-vec changed
-# after the capture; the line then reports traffic null and the capture as context.
-HV_TRAFFIC = {
-    "fma": {"p": 51, "bytes": 191.1e6, "current": False,
-            "note": "captured before the FP32 Gram moved to 32-row splits on a side stream"},
-    "tc": {"p": 51, "bytes": 183.4e6, "current": False,
-           "note": "captured before the tensor-core kernel rounded both TF32 halves and issued "
-                   "four products per step (same loads)"},
-}
+# Hess-vec) from one ncu capture at q = 80, per p; "current" is False when the
+# kernels changed after the capture (the line then reports traffic null).
+HV_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--q", type=int, default=80)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--engine", choices=["fma", "tc"], default="tc",
-                    help="gather GEMM of the FP32 Hessian-vector product: FP32 FMA kernel or "
-                         "tensor cores (tcgen05 kind::tf32, two-term TF32 operand split)")
+                    help="FP32 Hessian-vector product: FP32 FMA kernels or the TMA-fed "
+                         "tcgen05 engine (TF32 pairs, three products per step)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--hv-reps", type=int, default=30)
-    ap.add_argument("--solve-q", type=int, default=60,
-                    help="instance size of the full solve reported beside the headline (0 skips)")
-    ap.add_argument("--compare-q", type=int, default=40,
-                    help="instance size for the mixed-vs-FP64 solve comparison (0 skips it)")
+    ap.add_argument("--fp64-q", type=int, default=40,
+                    help="instance size of the mixed-vs-FP64 solve comparison (0 skips it)")
     ap.add_argument("--tcg-host", action="store_true",
                     help="launch the tCG kernels from the host instead of the device-driven graph "
                          "(same kernels; for profilers that list kernels one launch at a time)")
@@ -169,16 +166,17 @@ def bench_config(args, world):
     m = sum(math.comb(q, d) for d in range(5))
     return {"workload": f"dense BQP order-2 moment relaxation, q={q}, seed={args.seed}",
             "N": N, "m": m, "p0": int(math.ceil(math.log(m))), "precision": args.precision,
-            "hessvec_gemm": ("tensor cores (tcgen05 kind::tf32, operands split into two TF32 "
-                             "halves)" if args.engine == "tc" else "FP32 FMA"),
-            "step": "one ALM outer iteration of Algorithm 1, continuing one solve",
-            "l2": "working set > L2 (idx 42 MB + N x N FP64 multiplier and G, 84 MB each), no flush",
+            "hessvec_engine": ("tensor cores (TMA-fed tcgen05 kind::tf32, TF32 operand pairs, "
+                               "three products per step)" if args.engine == "tc" else "FP32 FMA"),
+            "step": "one full solve of Algorithm 1 from the seeded start to eta_max <= 1e-8",
+            "l2": "working set > L2 (idx 42 MB, N x N FP64 multiplier and G 84 MB each, "
+                  "tensor-core operand pairs 168 MB), no flush",
             "parallelism": f"replicas{world}"}
 
 
 def reduce_over_ranks(ms, steps_done, world, device):
     """Replicas: the job's timed-region length is the slowest rank's, and its
-    work is the sum of the outer iterations all ranks completed."""
+    work is the sum of the steps all ranks completed."""
     if world <= 1:
         return ms, steps_done
     import torch
@@ -191,7 +189,7 @@ def reduce_over_ranks(ms, steps_done, world, device):
 
 
 def job_value(ms_max, total_steps):
-    """Seconds per outer iteration of the whole job."""
+    """Seconds per step (one solve) of the whole job."""
     return ms_max / 1e3 / max(1, total_steps)
 
 
@@ -205,20 +203,25 @@ def workload(q, seed):
     return Q, c, N, m, idx, b, p0
 
 
-def hessvec_bytes(N, m, n_entries, n_pieces, p, fp_bytes):
-    """Algorithmic DRAM bytes of one Hessian-vector product (Proposition 4.2) in
-    the tiled form: the class-sum pass reads the slot map (4 B per upper-triangle
-    entry), writes and re-reads the class-ordered buffer (2 x fp_bytes per upper
-    entry), reads the piece table (8 B per piece) and writes w (fp_bytes per
-    class); the gather GEMM reads G (fp_bytes per entry) and the index map (4 B
-    per entry); Y, U are read and HU written once (8 B each, FP64 I/O)."""
-    return ((4 + 2 * fp_bytes) * n_entries + 8 * n_pieces + fp_bytes * m
-            + (fp_bytes + 4) * N * N + 3 * 8 * N * p)
+def hessvec_flops(N, p):
+    """Algorithmic flops of one Hessian-vector product (Proposition 4.2): the
+    SDDMM W = Y U' + U Y' on the N(N+1)/2 upper-triangle entries (2p multiply-adds
+    each) and the gather GEMM [G | A*(w)] [U ; Y] (2N multiply-adds per output):
+    2 N^2 p + 4 N^2 p."""
+    return 6.0 * N * N * p
+
+
+def hessvec_bytes(N, p, fp_bytes):
+    """Algorithmic DRAM bytes of one Hessian-vector product in its stored-G form:
+    G once (fp_bytes per entry) and the index map once per pass (4 bytes per
+    entry for the class sums over the upper triangle, 4 per entry for the
+    gather), w, Y, U L2-resident, HU written once (8 bytes per row element)."""
+    return (fp_bytes + 4) * N * N + 4 * N * (N + 1) / 2 + 8 * N * p
 
 
 def measure_hessvec(mds, torch, ctx, N, p, reps, precision, seed=11):
     """Mean device time of one Hessian-vector product at a random unit-row Y
-    (CUDA events on the library's stream, params.profile path)."""
+    (CUDA events on the library's stream)."""
     rng = np.random.default_rng(seed)
     Y = rng.standard_normal((N, p)); Y /= np.linalg.norm(Y, axis=1)[:, None]
     U = rng.standard_normal((N, p))
@@ -244,8 +247,9 @@ def measure_hessvec(mds, torch, ctx, N, p, reps, precision, seed=11):
 def cpu_baseline(q, seed, counts, budget_s):
     """The FP64 oracle, as it stands, on this host: time its Hessian-vector
     product, cost-plus-gradient evaluation and certificate matvec at the
-    workload's size, then scale by the operation counts of one outer iteration."""
-    from oracle import manidsdp as om, moment, operators as ops, subproblem as sp
+    workload's size and the GPU solve's mean factor width, then scale by the
+    operation counts of one solve."""
+    from oracle import manidsdp as om, moment, subproblem as sp
     from synthetic import bqp_instance, gaussian_factor
     t_setup = time.perf_counter()
     Q, c = bqp_instance(q, seed)
@@ -280,9 +284,9 @@ def cpu_baseline(q, seed, counts, budget_s):
         "sample": (f"oracle FP64 at q={q} (N={N}, m={m}, p={p}): {len(t_hv)} Hessian-vector products "
                    f"({hv:.3f} s each), {len(t_ev)} cost+gradient evaluations ({ev:.3f} s), "
                    f"{10 * len(t_mv)} certificate matvecs ({mv * 1e3:.1f} ms); value projects one "
-                   f"outer iteration from its counts (hessvecs={counts['hessvecs']:.0f}, "
-                   f"evals={counts['evals']:.0f}, lanczos matvecs={counts['lanczos_matvecs']:.0f}); "
-                   f"index-map setup {t_setup:.1f} s not included"),
+                   f"solve from the GPU solve's counts (hessvecs={counts['hessvecs']:.0f}, "
+                   f"evals={counts['evals']:.0f}, lanczos matvecs={counts['lanczos_matvecs']:.0f}, "
+                   f"mean p={counts['p']:.0f}); index-map setup {t_setup:.1f} s not included"),
     }
 
 
@@ -292,7 +296,8 @@ def run_reference(args):
         return
     steps = []
     cb = None
-    budget = max(2.0, min(args.cpu_sample_s, 60.0 / max(1, args.steps + args.warmup)))
+    # each step a bounded sample: the whole run stays within a few minutes
+    budget = max(1.0, min(args.cpu_sample_s, 120.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(args.q, args.seed, DEFAULT_COUNTS, budget)
         if i >= args.warmup:
@@ -309,6 +314,25 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def solve_once(mds, torch, ctx, Y0, p0, stream, Y_out=None):
+    """One step: a fresh solve (warm_start = 0) timed with CUDA events on the
+    library's stream; the final factor lands in the device buffer Y_out."""
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rep, p = mds.manidsdp_solve(ctx, Y0, p0, Y_out=Y_out)
+    e1.record(stream)
+    e1.synchronize()
+    return rep, p, e0.elapsed_time(e1)
 
 
 def main():
@@ -330,7 +354,6 @@ def main():
     Q, c, N, m, idx, b, p0 = workload(args.q, args.seed)
     prm = mds.manidsdp_default_params()
     prm.precision_mode = prec
-    prm.p_max = 256
     prm.profile = 2 if (args.hv_only and args.hv_stages) else 1
     prm.tensor_cores = 1 if args.engine == "tc" else 0
     if args.tcg_host:
@@ -343,144 +366,128 @@ def main():
         ms = measure_hessvec(mds, torch, ctx, N, p, args.hv_reps, prec)
         stages = mds.manidsdp_hessvec_stage_ms(ctx, True)
         calls = args.hv_reps + 3  # measure_hessvec's warm-up calls are staged too
-        fp_bytes = 4 if prec == mds.PREC_MIXED else 8
-        byt = hessvec_bytes(N, m, N * (N + 1) // 2, m, p, fp_bytes)
         out = {"hv_only": True, "q": args.q, "N": N, "p": p, "precision": args.precision,
-               "engine": args.engine,
-               "ms": ms, "gbs": byt / (ms * 1e-3) / 1e9,
-               "tflops": 6.0 * N * N * p / (ms * 1e-3) / 1e12}
+               "engine": args.engine, "ms": ms,
+               "gbs": hessvec_bytes(N, p, 4 if prec == mds.PREC_MIXED else 8) / (ms * 1e-3) / 1e9,
+               "tflops": hessvec_flops(N, p) / (ms * 1e-3) / 1e12}
         if args.hv_stages:
             out["stages_us"] = {k: round(v / calls * 1e3, 1) for k, v in stages.items()}
         print(json.dumps(out), flush=True)
         mds.manidsdp_destroy(ctx)
         return
     Y0 = torch.tensor(gaussian_factor(N, p0, args.seed + rank), device="cuda")
-    # warm-up: the first W outer iterations of a fresh solve
-    prm.max_outer = args.warmup
-    prm.warm_start = 0
-    mds.manidsdp_set_params(ctx, prm)
-    rep_w, _ = mds.manidsdp_solve(ctx, Y0, p0)
-    prm.max_outer = args.steps
-    prm.warm_start = 1
-    mds.manidsdp_set_params(ctx, prm)
+    for _ in range(args.warmup):
+        solve_once(mds, torch, ctx, Y0, p0, stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    Yout = torch.empty(N * prm.p_max, dtype=torch.float64, device="cuda")
     l0 = mds.manidsdp_launch_count()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    reps, ms_steps = [], []
     torch.cuda.nvtx.range_push("timed")  # lets a profiler restrict itself to the timed steps
-    rep, p_fin = mds.manidsdp_solve(ctx, Y0, p0)
+    for _ in range(args.steps):
+        rep, p_fin, ms1 = solve_once(mds, torch, ctx, Y0, p0, stream, Yout)
+        reps.append(rep)
+        ms_steps.append(ms1)
     torch.cuda.nvtx.range_pop()
-    e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     launches = mds.manidsdp_launch_count() - l0
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    steps_done = max(1, rep.outer)
-    ms, total_steps = reduce_over_ranks(ms, steps_done, world, "cuda")
+    ms = float(sum(ms_steps))
+    ms, total_steps = reduce_over_ranks(ms, args.steps, world, "cuda")
     value = job_value(ms, total_steps)
+    # tightness of the last timed solve: round its degree-1 moments to x in {-1,1}^q
+    rep_t, p_t = reps[-1], p_fin
+    tight = None
+    if rep_t.status == mds.OK:
+        Yf = Yout[: N * p_t].reshape(N, p_t).cpu().numpy()
+        S01 = Yf[1:args.q + 1] @ Yf[0]  # S[0, 1..q]: the degree-1 moments
+        x = np.where(S01 >= 0, 1.0, -1.0)
+        fx = float(x @ Q @ x + c @ x)
+        tight = {"f_xhat": fx, "value": rep_t.value, "p_final": p_t,
+                 "rel_gap": abs(fx - rep_t.value) / (1.0 + abs(rep_t.value)),
+                 "tight": abs(fx - rep_t.value) <= 1e-8 * (1.0 + abs(rep_t.value))}
 
-    # dominant kernel: the Hessian-vector product, live (phase events inside the
-    # timed solves) and in isolation at p = p_0
-    hv_ms_live = rep.ms_hessvec / max(1, rep.hessvecs)
-    p_avg = rep.hessvec_p_sum / max(1, rep.hessvecs)
-    fp_bytes = 4 if prec == mds.PREC_MIXED else 8
-    n_entries = N * (N + 1) // 2
-    n_pieces = m + 2 * (args.q - 1) * 2 + (N + 31) // 32  # classes + extra pieces of long classes
-    bytes_live = hessvec_bytes(N, m, n_entries, n_pieces, p_avg, fp_bytes)
-    flops_live = 6.0 * N * N * p_avg
-    hv_ms_iso = measure_hessvec(mds, torch, ctx, N, p0, args.hv_reps, prec)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    if prec == mds.PREC_MIXED:
-        tr = HV_TRAFFIC.get(args.engine)
-        roof = {"bound": "hbm", "achieved": bytes_live / (hv_ms_live * 1e-3) / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "traffic": tr["bytes"] if tr and tr["current"] else None,
-                "traffic_last_capture": tr, "peak_source": peak_src,
-                "kernel": "Hessian-vector product (FP32 class means + gather GEMM + epilogue)",
-                "avg_ms": hv_ms_live, "p_avg": p_avg,
-                "isolated_ms_at_p0": hv_ms_iso,
-                "isolated_gbs_at_p0": hessvec_bytes(N, m, n_entries, n_pieces, p0, 4) / (hv_ms_iso * 1e-3) / 1e9,
-                "alu_tflops": flops_live / (hv_ms_live * 1e-3) / 1e12}
+    # dominant work: the Hessian-vector products, timed live (phase events inside
+    # the timed solves)
+    hv_ms_total = sum(r.ms_hessvec for r in reps)
+    hv_count = sum(r.hessvecs for r in reps)
+    p_avg = sum(r.hessvec_p_sum for r in reps) / max(1, hv_count)
+    hv_ms = hv_ms_total / max(1, hv_count)
+    peaks = load_peaks()
+    flops = hessvec_flops(N, p_avg)
+    byts = hessvec_bytes(N, p_avg, 4 if prec == mds.PREC_MIXED else 8)
+    if prec == mds.PREC_MIXED and args.engine == "tc":
+        # kernel timed inside a long step: the sustained bf16 figure, TF32 at half of it
+        if "bf16_tflops_sustained" in peaks:
+            peak, src = peaks["bf16_tflops_sustained"] * 0.5, "measured (bf16 sustained x 1/2 for TF32)"
+        else:
+            peak, src = 1700.0 * 0.5, "fallback (bf16 sustained x 1/2 for TF32)"
+        roof = {"bound": "tensor", "achieved": flops / (hv_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": src}
+    elif prec == mds.PREC_MIXED:
+        roof = {"bound": "hbm", "achieved": byts / (hv_ms * 1e-3) / 1e9,
+                "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     else:
         fp64_peak = 1.19  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x ~1.95 GHz, probe-measured
-        roof = {"bound": "alu", "achieved": flops_live / (hv_ms_live * 1e-3) / 1e12, "peak": fp64_peak,
-                "unit": "TFLOP/s", "traffic": None, "peak_source": "FP64 FMA probe on GB300",
-                "kernel": "Hessian-vector product (FP64)", "avg_ms": hv_ms_live, "p_avg": p_avg}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        roof = {"bound": "alu", "achieved": flops / (hv_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "peak_source": "FP64 FMA probe on GB300"}
+    tr = HV_TRAFFIC.get(args.engine)
+    roof.update({"frac": roof["achieved"] / roof["peak"],
+                 "traffic": tr["bytes"] if tr and tr.get("current") else None,
+                 "kernel": "Hessian-vector product (SDDMM class sums + gather GEMM + epilogue)",
+                 "avg_ms": hv_ms, "p_avg": p_avg, "hessvecs_per_solve": hv_count / len(reps),
+                 "algorithmic_flops": flops, "algorithmic_bytes": byts,
+                 "hbm_gbs": byts / (hv_ms * 1e-3) / 1e9})
 
     e2e = None
     if not args.no_e2e:
         # the user's call from host memory: setup from the host index map and b, a
-        # solve of W + K outer iterations from a host start, host outputs; all host
-        # buffers pinned, inputs generated before the timed region
+        # full solve from a host start, host outputs; pinned host buffers, inputs
+        # generated before the timed region
         pe = mds.manidsdp_default_params()
         pe.precision_mode = prec
         pe.tensor_cores = prm.tensor_cores
-        pe.max_outer = args.warmup + args.steps
         idx_h = torch.from_numpy(idx).pin_memory()
         b_h = torch.from_numpy(b).pin_memory()
         Y0h = torch.from_numpy(gaussian_factor(N, p0, args.seed + rank)).pin_memory()
         y_host = torch.empty(m, dtype=torch.float64).pin_memory()
-        Yout = torch.empty(N * pe.p_max, dtype=torch.float64).pin_memory()
+        z_host = torch.empty(N, dtype=torch.float64).pin_memory()
+        Yh = torch.empty(N * pe.p_max, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2 = mds.manidsdp_setup(N, m, idx_h, b_h, params=pe, stream=stream.cuda_stream)
-        rep2, p2 = mds.manidsdp_solve(ctx2, Y0h, p0, Y_out=Yout, y_out=y_host)
+        rep2, p2 = mds.manidsdp_solve(ctx2, Y0h, p0, Y_out=Yh, y_out=y_host, z_out=z_host)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         mds.manidsdp_destroy(ctx2)
-        steps2 = max(1, rep2.outer)
-        e2e = {"value": t_e2e / steps2, "unit": UNIT,
-               "h2d_bytes_per_step": int((idx.nbytes + b.nbytes + Y0h.numel() * 8) / steps2),
-               "d2h_bytes_per_step": int((m * 8 + N * p2 * 8) / steps2),
-               "includes": f"setup (index-map validation, inverse map, H2D) + {rep2.outer} outer "
-                           "iterations from a pinned host start + D2H of y and Y into pinned "
-                           "buffers, per outer iteration"}
-
-    solve60 = None
-    if rank == 0 and args.solve_q > 0:
-        Qs, cs, Ns, ms_, idxs, bs, p0s = workload(args.solve_q, args.seed)
-        ps = mds.manidsdp_default_params()
-        ps.precision_mode = prec
-        ps.tensor_cores = prm.tensor_cores
-        cs_ = mds.manidsdp_setup(Ns, ms_, idxs, bs, params=ps, stream=stream.cuda_stream)
-        Y0s = torch.tensor(gaussian_factor(Ns, p0s, args.seed), device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rs, _ = mds.manidsdp_solve(cs_, Y0s, p0s)
-        torch.cuda.synchronize()
-        solve60 = {"q": args.solve_q, "N": Ns, "m": ms_, "s": time.perf_counter() - t0,
-                   "eta_max": rs.eta_max, "value": rs.value, "outer": rs.outer,
-                   "hessvecs": rs.hessvecs, "converged": rs.status == mds.OK}
-        mds.manidsdp_destroy(cs_)
+        e2e = {"value": t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(idx.nbytes + b.nbytes + Y0h.numel() * 8),
+               "d2h_bytes_per_step": int(m * 8 + N * 8 + N * p2 * 8),
+               "eta_max": rep2.eta_max, "converged": rep2.status == mds.OK,
+               "includes": "setup (index-map validation, inverse map, H2D of idx and b) + one "
+                           "solve from a pinned host start + D2H of y, z and Y into pinned buffers"}
 
     compare = None
-    if rank == 0 and args.compare_q > 0:
+    if rank == 0 and args.fp64_q > 0:
         # the same instance solved by the mixed form and by the plain FP64 form
-        Qc, cc_, Nc, mc, idxc, bc, p0c = workload(args.compare_q, args.seed)
+        Qc, cc_, Nc, mc, idxc, bc, p0c = workload(args.fp64_q, args.seed)
         Y0c = torch.tensor(gaussian_factor(Nc, p0c, args.seed), device="cuda")
-        compare = {"q": args.compare_q, "N": Nc}
+        compare = {"q": args.fp64_q, "N": Nc}
         for name, pm in (("mixed", mds.PREC_MIXED), ("fp64", mds.PREC_FP64)):
             pc = mds.manidsdp_default_params()
             pc.precision_mode = pm
             pc.tensor_cores = prm.tensor_cores
             cx = mds.manidsdp_setup(Nc, mc, idxc, bc, params=pc, stream=stream.cuda_stream)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, _ = mds.manidsdp_solve(cx, Y0c, p0c)
-            torch.cuda.synchronize()
-            compare[name] = {"s": time.perf_counter() - t0, "eta_max": rc.eta_max,
-                             "value": rc.value, "outer": rc.outer, "hessvecs": rc.hessvecs}
+            rc, _, msc = solve_once(mds, torch, cx, Y0c, p0c, stream)
+            compare[name] = {"s": msc / 1e3, "eta_max": rc.eta_max, "value": rc.value,
+                             "outer": rc.outer, "hessvecs": rc.hessvecs,
+                             "converged": rc.status == mds.OK}
             mds.manidsdp_destroy(cx)
         compare["speedup_mixed_over_fp64"] = compare["fp64"]["s"] / compare["mixed"]["s"]
         compare["value_rel_diff"] = abs(compare["fp64"]["value"] - compare["mixed"]["value"]) / abs(
@@ -488,25 +495,33 @@ def main():
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        counts = dict(hessvecs=rep.hessvecs / steps_done, evals=rep.evals / steps_done,
-                      grads=rep.grads / steps_done, lanczos_matvecs=rep.lanczos_matvecs / steps_done,
-                      p=p_avg)
+        counts = dict(hessvecs=hv_count / len(reps), evals=sum(r.evals for r in reps) / len(reps),
+                      grads=sum(r.grads for r in reps) / len(reps),
+                      lanczos_matvecs=sum(r.lanczos_matvecs for r in reps) / len(reps), p=p_avg)
         cb = cpu_baseline(args.q, args.seed, counts, args.cpu_sample_s)
 
     mds.manidsdp_destroy(ctx)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / steps_done, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/f64 (FP32 Hessian-vector products, FP64 elsewhere)" if prec == mds.PREC_MIXED else "f64",
+            "warmup": args.warmup, "ms_per_step": ms / max(1, total_steps) * world,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32/f64 (TF32-pair tensor-core Hessian-vector products, df64 cost and "
+                      "gradient, FP64 multiplier, KKT residuals and Lanczos)"
+                      if prec == mds.PREC_MIXED else "f64"),
             "data": "synthetic (seeded N(0,1) Q, c; seeded Gaussian start)",
             "config": bench_config(args, world),
-            "steps_done": steps_done, "eta_max_after": rep.eta_max, "value_after": rep.value,
-            "outer_total": args.warmup + rep.outer, "full_solve": solve60,
-            "rtr_iters": rep.rtr_iters, "hessvecs": rep.hessvecs, "p_final": rep.p,
-            "phase_ms": {"hessvec": rep.ms_hessvec, "eval": rep.ms_eval, "grad": rep.ms_grad,
-                         "lanczos_wall": rep.ms_lanczos},
+            "solves": [{"s": t / 1e3, "eta_max": r.eta_max, "value": r.value, "outer": r.outer,
+                        "hessvecs": r.hessvecs, "converged": r.status == mds.OK}
+                       for r, t in zip(reps, ms_steps)],
+            "all_converged": all(r.status == mds.OK and r.eta_max <= 1e-8 for r in reps),
+            "tightness": tight,
+            "phase_ms_per_solve": {
+                "hessvec": hv_ms_total / len(reps),
+                "eval": sum(r.ms_eval for r in reps) / len(reps),
+                "grad": sum(r.ms_grad for r in reps) / len(reps),
+                "lanczos": sum(r.ms_lanczos for r in reps) / len(reps),
+                "rank_update_host": sum(r.ms_rank for r in reps) / len(reps)},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
             "mixed_vs_fp64": compare,
             "clocks": clk,

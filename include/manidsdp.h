@@ -83,6 +83,11 @@ typedef struct {
   double carry_t0;        /* first step of the carried-direction line search; <= 0: sqrt(N) */
   double round_eta;       /* try the rank-one rounding after outer iterations with
                              eta_max <= round_eta (0 disables it) */
+  double tc_lowprec_eta;  /* precision schedule of the tensor-core Hess-vec: while the
+                             previous outer iteration's eta_max exceeds this value the
+                             products use single TF32 operands (about 2^-11 relative
+                             per operand) instead of TF32 pairs; 0 (default): pairs
+                             throughout */
   int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 512 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
   int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */

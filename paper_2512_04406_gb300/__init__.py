@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "sigma0", "sigma_min", "sigma_max", "gamma", "kappa1", "kappa2", "tol",
         "tol_grad_min", "tol_grad_max", "tol_grad_factor", "rank_tol", "neg_tol", "tcg_floor",
-        "tcg_abs", "carry_t0", "round_eta")] + [
+        "tcg_abs", "carry_t0", "round_eta", "tc_lowprec_eta")] + [
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
             "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile", "tcg_device",

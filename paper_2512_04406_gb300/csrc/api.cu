@@ -101,6 +101,7 @@ struct manidsdp_ctx {
   float *Yxh = nullptr, *Yxl = nullptr, *Uxh = nullptr, *Uxl = nullptr;    // N x ld(p)
   float *YTh = nullptr, *YTl = nullptr, *UTh = nullptr, *UTl = nullptr;    // p x ldg
   float* Wfull = nullptr;  // W = Y Up' + Up Y' at every entry (N x ldg)
+  int tc_pairs = 1;        // 1: TF32 pairs (three products); 0: single TF32 products
   int2* tiles = nullptr;  // upper-triangle 128 x 128 tile pairs of the SDDMM
   int ntiles = 0;
   bool resume_have_U = false;  // the last iteration augmented Y = [Y, 0] and set U = [0, V]
@@ -122,7 +123,7 @@ struct manidsdp_ctx {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct Graph {
-    int p, prec;
+    int p, prec, pairs;
     double sigma;
     const void *Y, *G;
     cudaGraph_t graph;
@@ -220,13 +221,13 @@ int hessvec_tcx(manidsdp_ctx* c, int p, cudaStream_t s, const std::function<void
   launch_tcx_split_rows(N, p, c->Up, c->Uxh, c->Uxl, ldp, c->UTh, c->UTl, ldg, s);
   if (mark) mark(1);
   launch_tcx_sddmm(N, p, c->Yxh, c->Yxl, c->Uxh, c->Uxl, ldp, c->slot, c->perm, c->Wfull, ldg,
-                   c->tiles, c->ntiles, c->tc_err, s);
+                   c->tiles, c->ntiles, c->tc_err, s, c->tc_pairs);
   launch_piece_sums(c->cm, c->perm, c->mult, reinterpret_cast<float*>(c->piece_buf), c->wf, s);
   if (mark) mark(2);
   launch_tcx_split_matrix(N, c->Wfull, c->idx, c->wf, float(c->sigma), c->QWhi, c->QWlo, ldg, s);
   const int S = launch_tcx_gather(N, p, c->Ghi, c->Glo, c->QWhi, c->QWlo, ldg, c->UTh, c->UTl,
                                   c->YTh, c->YTl, ldg, static_cast<float*>(c->gws), c->gws_bytes,
-                                  c->tc_err, s);
+                                  c->tc_err, s, c->tc_pairs);
   if (mark) {
     mark(3);
     mark(4);
@@ -532,6 +533,7 @@ void default_params(manidsdp_params* p) {
   p->tcg_abs = 0.1;
   p->carry_t0 = 0.0;
   p->round_eta = 1e-2;
+  p->tc_lowprec_eta = 0.0;
   p->warm_start = 0;
   p->p0 = 2;
   p->p_min = 2;
@@ -558,7 +560,7 @@ bool params_ok(const manidsdp_params& p) {
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
          flag(p.tcg_device) && flag(p.warm_start) && flag(p.tensor_cores) &&
          p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
-         p.tol > 0.0;
+         p.tol > 0.0 && p.tc_lowprec_eta >= 0.0;
 }
 
 struct NonFinite {};
@@ -1027,7 +1029,9 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
   const void* Gkey = prec == MANIDSDP_PREC_MIXED ? static_cast<const void*>(g32(c))
                                                  : static_cast<const void*>(c->G);
   for (auto& g : c->graphs)
-    if (g.p == p && g.prec == prec && g.sigma == c->sigma && g.Y == c->Y && g.G == Gkey) return g;
+    if (g.p == p && g.prec == prec && g.sigma == c->sigma && g.Y == c->Y && g.G == Gkey &&
+        g.pairs == c->tc_pairs)
+      return g;
   if (c->graphs.size() >= 4) drop_graphs(c);
   const int N = c->N;
   const size_t n = size_t(N) * p;
@@ -1037,6 +1041,7 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
   G.sigma = c->sigma;
   G.Y = c->Y;
   G.G = Gkey;
+  G.pairs = c->tc_pairs;
   MDS_CUDA(cudaGraphCreate(&G.graph, 0));
   cudaGraphConditionalHandle h;
   MDS_CUDA(cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault));
@@ -1210,8 +1215,11 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     }
     bool have_U = resume && c->resume_have_U;
     int U_cols = have_U ? c->resume_U_cols : 0;
+    double eta_prev = INFINITY;
     for (int k = 0; k < P.max_outer; ++k) {
       c->sigma = sigma;
+      // precision schedule: single TF32 products while eta_max is above tc_lowprec_eta
+      c->tc_pairs = (P.tc_lowprec_eta > 0.0 && eta_prev > P.tc_lowprec_eta) ? 0 : 1;
       // step 3a: the carried direction U = [0, V]
       if (have_U) {
         double f0, r2;
@@ -1284,6 +1292,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       rep.outer = k + 1;
       rep.p = p;
       const double eta = std::max(rep.eta_p, std::max(rep.eta_d, rep.eta_g));
+      eta_prev = eta;
       if (P.verbose)
         std::fprintf(stderr,
                      "[manidsdp] k=%d p=%d sigma=%.3g rtr=%d(rej %d, bnd %d, D %.2e) gnorm=%.3e "
@@ -1399,6 +1408,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       }
     }
     c->sigma = sigma;
+    c->tc_pairs = 1;
     c->resume_valid = true;
     c->resume_p = p;  // columns of c->Y now (after rank drop and augmentation)
     c->resume_rscale = rscale;

@@ -123,17 +123,19 @@ void launch_tcx_split_rows(int N, int p, const double* X, float* hi, float* lo, 
 void launch_tcx_split_matrix(int N, const float* G, const int32_t* idx, const float* w,
                              float gscale, float* hi, float* lo, int ld, cudaStream_t s);
 // Split-K partials [splits][N][p] of T = G Up + QW Y (QW = sigma Q(W)) from TF32 pairs;
-// returns the number of splits, tcx_gather_splits(N).
+// returns the number of splits, tcx_gather_splits(N).  pairs = 0: only the hi parts, one TF32 product per step (about 2^-11 relative
+// per operand; the precision schedule's early iterations).
 int tcx_gather_splits(int N);
 int launch_tcx_gather(int N, int p, const float* Ghi, const float* Glo, const float* QWhi,
                       const float* QWlo, int ldg, const float* UThi, const float* UTlo,
                       const float* YThi, const float* YTlo, int ldt, float* part, size_t ws_bytes,
-                      int* err, cudaStream_t s);
+                      int* err, cudaStream_t s, int pairs = 1);
 // W = Y U' + U Y' on the upper-triangle tiles: entry (r <= c) weighted 2 off the
 // diagonal written to perm[slot[r N + c]], and every entry of W into wfull (ldw).
 void launch_tcx_sddmm(int N, int p, const float* Yhi, const float* Ylo, const float* Uhi,
                       const float* Ulo, int ld, const int32_t* slot, float* perm, float* wfull,
-                      int ldw, const int2* tiles, int ntiles, int* err, cudaStream_t s);
+                      int ldw, const int2* tiles, int ntiles, int* err, cudaStream_t s,
+                      int pairs = 1);
 std::vector<int2> tcx_upper_tiles(int N);
 // Per-piece sums of the class-ordered buffer into out[a] / mult[a] (kernels_sddmm.cu).
 void launch_piece_sums(const ClassMap& cm, const float* perm, const double* mult,

@@ -59,6 +59,7 @@ struct TcxArgs {
   int kchunk;         // K values per CTA (split-K), a multiple of kXBK
   int nacc;           // TMEM accumulators per CTA (chains of <= kXChain each)
   int mode;           // 0: partial product out[split][M][ldo]; 1: SDDMM scatter
+  int pairs;          // 1: TF32 pairs, three products per step; 0: hi parts only, one product
   float* out;
   int ldo;
   const int32_t* slot;  // mode 1: N x N slot map; perm: class-ordered buffer
@@ -172,13 +173,19 @@ __device__ __forceinline__ void x_tmem_ld16(uint32_t taddr, float* v) {
 }
 
 
+// BK K-values per stage: 32, 128-byte rows with the 128-byte swizzle (16, 64-byte
+// rows with the 64-byte swizzle, measured slower: not instantiated).
+template <int BK>
 __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constant__ TcxArgs P,
                                                             int nstage) {
   extern __shared__ __align__(1024) unsigned char x_smem[];
+  constexpr uint32_t kAtom = 8 * BK * 4;             // 8-row swizzle atom (bytes)
+  constexpr uint32_t kSwz = BK == 32 ? 2u : 4u;      // descriptor swizzle mode
   const int bn = P.bn;
-  const int a_bytes = kXBM * kXBK * 4;  // one A tile (hi or lo): 128 rows of 128 bytes
-  const int b_bytes = bn * kXBK * 4;    // one B tile
-  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const int a_bytes = kXBM * BK * 4;  // one A tile (hi or lo)
+  const int b_bytes = bn * BK * 4;    // one B tile
+  const int nt = P.pairs ? 2 : 1;     // tiles per operand
+  const int stage_bytes = nt * (a_bytes + b_bytes);
   // 1024-byte aligned working area (the swizzle pattern repeats every 1024 bytes)
   const uint32_t sraw = smem_u32(x_smem);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constan
   }
   const int kb = split * P.kchunk;
   const int ke = min(P.ktot, kb + P.kchunk);
-  const int nst = ke > kb ? (ke - kb) / kXBK : 0;
+  const int nst = ke > kb ? (ke - kb) / BK : 0;
   const int per_chain = (nst + P.nacc - 1) / max(1, P.nacc);
   int ncols_alloc = 32;
   while (ncols_alloc < P.nacc * bn) ncols_alloc <<= 1;
@@ -240,15 +247,17 @@ __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constan
       }
       if (counts[2]) break;
       x_bar_expect_tx(&full[s], uint32_t(stage_bytes));
-      const int k = kb + it * kXBK;
+      const int k = kb + it * BK;
       int seg = 0;
       while (seg + 1 < kXSeg && k >= P.koff[seg + 1]) ++seg;
       const int kl = k - P.koff[seg];
       const uint32_t st = sbase + uint32_t(s * stage_bytes);
       x_tma2d(st, &P.a_hi[seg], kl, m0, &full[s]);
-      x_tma2d(st + uint32_t(a_bytes), &P.a_lo[seg], kl, m0, &full[s]);
-      x_tma2d(st + uint32_t(2 * a_bytes), &P.b_hi[seg], kl, n0, &full[s]);
-      x_tma2d(st + uint32_t(2 * a_bytes + b_bytes), &P.b_lo[seg], kl, n0, &full[s]);
+      x_tma2d(st + uint32_t(nt * a_bytes), &P.b_hi[seg], kl, n0, &full[s]);
+      if (P.pairs) {
+        x_tma2d(st + uint32_t(a_bytes), &P.a_lo[seg], kl, m0, &full[s]);
+        x_tma2d(st + uint32_t(2 * a_bytes + b_bytes), &P.b_lo[seg], kl, n0, &full[s]);
+      }
       counts[0] = it + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -267,17 +276,21 @@ __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constan
       const uint32_t acc = tmem + uint32_t(chain * bn);
       const uint32_t st = sbase + uint32_t(s * stage_bytes);
       const uint32_t ahi = st, alo = st + a_bytes;
-      const uint32_t bhi = st + 2 * a_bytes, blo = bhi + b_bytes;
+      const uint32_t bhi = st + nt * a_bytes, blo = bhi + b_bytes;
 #pragma unroll
-      for (int ks = 0; ks < kXBK / 8; ++ks) {
-        // K step of 8 values = a 32-byte offset inside the 128-byte swizzle atom;
-        // row-adjacent 8-row atoms 1024 bytes apart
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        // K step of 8 values = a 32-byte offset inside the swizzled row;
+        // row-adjacent 8-row atoms kAtom bytes apart
         const uint32_t o = uint32_t(ks * 32);
-        const uint64_t dah = x_desc(ahi + o, 16, 1024, 2), dal = x_desc(alo + o, 16, 1024, 2);
-        const uint64_t dbh = x_desc(bhi + o, 16, 1024, 2), dbl = x_desc(blo + o, 16, 1024, 2);
-        x_mma(acc, dal, dbh, idesc, (first && ks == 0) ? 0u : 1u);
-        x_mma(acc, dah, dbl, idesc, 1u);
-        x_mma(acc, dah, dbh, idesc, 1u);
+        const uint64_t dah = x_desc(ahi + o, 16, kAtom, kSwz), dal = x_desc(alo + o, 16, kAtom, kSwz);
+        const uint64_t dbh = x_desc(bhi + o, 16, kAtom, kSwz), dbl = x_desc(blo + o, 16, kAtom, kSwz);
+        if (P.pairs) {
+          x_mma(acc, dal, dbh, idesc, (first && ks == 0) ? 0u : 1u);
+          x_mma(acc, dah, dbl, idesc, 1u);
+          x_mma(acc, dah, dbh, idesc, 1u);
+        } else {
+          x_mma(acc, dah, dbh, idesc, (first && ks == 0) ? 0u : 1u);
+        }
       }
       x_commit(&empty[s]);
       counts[1] = it + 1;
@@ -316,11 +329,6 @@ __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constan
         if (P.mode == 1) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) tile[rl * 129 + c0 + i] = v[i];
-          if (row < P.M) {  // W[row, n0 + c0 ..] for the full matrix
-            float* dst = P.wfull + size_t(row) * P.ldw + n0 + c0;
-            for (int i = 0; i < 16; ++i)
-              if (n0 + c0 + i < P.ncol) dst[i] = v[i];
-          }
           continue;
         }
         if (row >= P.M) continue;
@@ -336,18 +344,22 @@ __global__ void __launch_bounds__(kXThreads, 1) tcx3_kernel(const __grid_constan
         }
       }
       if (P.mode == 1) {
-        // the 128 epilogue threads, one column each: slot reads coalesced along
-        // rows, sixteen in flight per thread before their scattered writes
+        // the 128 epilogue threads, one column t each: the tile's rows into W
+        // (and, off the diagonal, its columns into the mirrored rows of W) with
+        // coalesced stores, then the upper-triangle entries to their class slots,
+        // sixteen slot reads in flight per thread before the scattered writes
         asm volatile("bar.sync 1, 128;" ::: "memory");
         const int t = tid - 64;
         const int col = n0 + t;
-        if (col < P.ncol && n0 != m0) {  // the mirrored tile: row col of W
-          float* dst = P.wfull + size_t(col) * P.ldw + m0;
-          const int rn = min(kXBM, P.M - m0);
-          for (int r = 0; r < rn; ++r) dst[r] = tile[r * 129 + t];
+        const int rn = min(kXBM, P.M - m0);
+        if (col < P.ncol)
+          for (int r = 0; r < rn; ++r) P.wfull[size_t(m0 + r) * P.ldw + col] = tile[r * 129 + t];
+        if (n0 != m0 && m0 + t < P.M) {
+          const int cn = min(kXBM, P.ncol - n0);
+          for (int r = 0; r < cn; ++r) P.wfull[size_t(n0 + r) * P.ldw + m0 + t] = tile[t * 129 + r];
         }
         if (col < P.ncol) {
-          const int rmax = min(kXBM, min(P.M - m0, col - m0 + 1));  // rows r <= col
+          const int rmax = min(rn, col - m0 + 1);  // rows r <= col
           for (int r0 = 0; r0 < rmax; r0 += 16) {
             int sl[16];
 #pragma unroll
@@ -472,37 +484,46 @@ EncodeTiled x_encoder() {
 // multiple of 4): boxes of 32 columns (128 bytes) x box_rows rows with the
 // 128-byte swizzle; reads outside the matrix fill zeros.
 void x_map(CUtensorMap* m, const float* base, int rows, int cols, int ld, int box_rows) {
+  const int bk = kXBK;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld & 3) != 0 || box_rows < 1 ||
       box_rows > 256 || rows < 1 || cols < 1 || ld < cols)
     throw DeviceError{cudaErrorInvalidValue};
   const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
   const cuuint64_t strides[1] = {cuuint64_t(ld) * sizeof(float)};
-  const cuuint32_t box[2] = {uint32_t(kXBK), cuuint32_t(box_rows)};
+  const cuuint32_t box[2] = {uint32_t(bk), cuuint32_t(box_rows)};
   const cuuint32_t estr[2] = {1u, 1u};
   const CUresult r = x_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base),
                                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                 bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw DeviceError{cudaErrorInvalidValue};
 }
 
-int x_stage_bytes(int bn) { return 2 * kXBM * kXBK * 4 + 2 * bn * kXBK * 4; }
-int x_stages(int bn) { return std::max(2, std::min(6, (200 * 1024) / x_stage_bytes(bn))); }
+int x_stage_bytes(int bn, int bk, int pairs) {
+  return (pairs ? 2 : 1) * (kXBM * bk * 4 + bn * bk * 4);
+}
+int x_stages(int bn, int bk, int pairs) {
+  return std::max(2, std::min(8, (200 * 1024) / x_stage_bytes(bn, bk, pairs)));
+}
 // stages + barriers + the 1024-byte alignment slack
-size_t x_smem_bytes(int bn, int nstage) { return size_t(nstage) * x_stage_bytes(bn) + 256 + 1024; }
+size_t x_smem_bytes(int bn, int bk, int pairs, int nstage) {
+  return size_t(nstage) * x_stage_bytes(bn, bk, pairs) + 256 + 1024;
+}
 
 void x_launch(const TcxArgs& a, dim3 grid, cudaStream_t s) {
-  const int nst = x_stages(a.bn);
-  const size_t smem = x_smem_bytes(a.bn, nst);
+  const int nst = x_stages(a.bn, kXBK, a.pairs);
+  const size_t smem = x_smem_bytes(a.bn, kXBK, a.pairs, nst);
   static std::once_flag once;
   std::call_once(once, [] {
     size_t mx = 0;
-    for (int bn = 16; bn <= 256; bn += 16) mx = std::max(mx, x_smem_bytes(bn, x_stages(bn)));
-    MDS_CUDA(cudaFuncSetAttribute(tcx3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    for (int bn = 16; bn <= 256; bn += 16)
+      for (int pr : {0, 1}) mx = std::max(mx, x_smem_bytes(bn, kXBK, pr, x_stages(bn, kXBK, pr)));
+    MDS_CUDA(cudaFuncSetAttribute(tcx3_kernel<kXBK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(mx)));
   });
   count_launches(1);
-  tcx3_kernel<<<grid, kXThreads, smem, s>>>(a, nst);
+  tcx3_kernel<kXBK><<<grid, kXThreads, smem, s>>>(a, nst);
   MDS_CUDA(cudaGetLastError());
 }
 
@@ -535,7 +556,7 @@ int tcx_gather_splits(int N) { return (2 * round_up(N, kXBK) + kXChain - 1) / kX
 int launch_tcx_gather(int N, int p, const float* Ghi, const float* Glo, const float* QWhi,
                       const float* QWlo, int ldg, const float* UThi, const float* UTlo,
                       const float* YThi, const float* YTlo, int ldt, float* part, size_t ws_bytes,
-                      int* err, cudaStream_t s) {
+                      int* err, cudaStream_t s, int pairs) {
   if (p < 1 || p > kMaxP) throw DeviceError{cudaErrorInvalidValue};
   TcxArgs a{};
   const int bn = x_bn(p);
@@ -559,6 +580,7 @@ int launch_tcx_gather(int N, int p, const float* Ghi, const float* Glo, const fl
   a.kchunk = kXChain;
   a.nacc = 1;
   a.mode = 0;
+  a.pairs = pairs;
   a.out = part;
   a.ldo = p;
   a.err = err;
@@ -570,7 +592,8 @@ int launch_tcx_gather(int N, int p, const float* Ghi, const float* Glo, const fl
 
 void launch_tcx_sddmm(int N, int p, const float* Yhi, const float* Ylo, const float* Uhi,
                       const float* Ulo, int ld, const int32_t* slot, float* perm, float* wfull,
-                      int ldw, const int2* tiles, int ntiles, int* err, cudaStream_t s) {
+                      int ldw, const int2* tiles, int ntiles, int* err, cudaStream_t s,
+                      int pairs) {
   if (p < 1 || p > kMaxP) throw DeviceError{cudaErrorInvalidValue};
   TcxArgs a{};
   // segment 0: Y Up' (A = Y, B = Up); segment 1: Up Y'
@@ -593,6 +616,7 @@ void launch_tcx_sddmm(int N, int p, const float* Yhi, const float* Ylo, const fl
   a.kchunk = a.ktot;
   a.nacc = (a.ktot + kXChain - 1) / kXChain;  // <= 2 for p <= 512
   a.mode = 1;
+  a.pairs = pairs;
   a.slot = slot;
   a.perm = perm;
   a.wfull = wfull;

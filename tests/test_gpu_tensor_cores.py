@@ -1,13 +1,15 @@
-"""The tensor-core gather GEMM of the FP32 Hessian-vector product
-(params.tensor_cores = 1: tcgen05 kind::tf32 with each operand split into two
-TF32 halves, four products per step) against the FP64 oracle (Proposition 4.2, Eq. (4.7)) and against
-the FP32 FMA kernel, through the C ABI.
+"""The tensor-core engine of the FP32 Hessian-vector product (params.tensor_cores
+= 1: TMA-fed tcgen05 kind::tf32 SDDMM and gather GEMM on TF32 operand pairs,
+three products per step) against the FP64 oracle (Proposition 4.2, Eq. (4.7))
+and against the FP32 FMA kernels, through the C ABI.
 
 Tolerances: the mixed-form Hessian-vector product's 5e-5 relative against the
-oracle, for both FP32 engines and between them (the split represents each
-operand to 2^-23, about FP32's own accuracy, but the sums of 2N products cancel
-in Eq. (4.7), so the engines differ by ~1e-5 at N = 3241).  A solve with the tensor-core
-engine meets the solver bar: eta_max <= 1e-8, value within 1e-9 of the oracle.
+oracle, for both FP32 engines and between them (the pairs represent each
+operand to 2^-23, about FP32's own accuracy; the tensor core's FP32 accumulation
+over chains of up to 640 K-values costs ~1e-5 at N = 3241).  A solve with the
+tensor-core engine meets the solver bar: eta_max <= 1e-8, value within 1e-9 of
+the oracle, also under the precision schedule (single TF32 products while
+eta_max > tc_lowprec_eta).
 """
 import numpy as np
 import pytest
@@ -51,7 +53,7 @@ def hessvec_both_engines(torch, inst, p, seed, sigma=1.3, xt_scale=0.3):
 
 
 @pytest.mark.parametrize("q,p", [(1, 1), (3, 2), (6, 3), (10, 5), (20, 7), (20, 16), (20, 33),
-                                 (20, 130), (20, 256)])
+                                 (20, 130), (20, 256), (20, 300), (20, 512)])
 def test_tensor_core_hessvec_small(torch, q, p):
     inst = instance(q, seed=q)
     H_tc, H_tc2, H_fma, H_ref = hessvec_both_engines(torch, inst, p, seed=q + p)
@@ -61,7 +63,7 @@ def test_tensor_core_hessvec_small(torch, q, p):
     assert relerr(H_tc, H_fma) <= 5e-5
 
 
-@pytest.mark.parametrize("p", [15, 100, 256])
+@pytest.mark.parametrize("p", [15, 100, 256, 330, 512])
 def test_tensor_core_hessvec_q80(torch, p):
     inst = instance(80, seed=0)
     H_tc, _, H_fma, H_ref = hessvec_both_engines(torch, inst, p, seed=p, sigma=2.5, xt_scale=0.05)
@@ -71,13 +73,15 @@ def test_tensor_core_hessvec_q80(torch, p):
     assert relerr(H_tc, H_fma) <= 5e-5
 
 
-@pytest.mark.parametrize("q,seed,tcg_device", [(8, 1, 1), (12, 3, 1), (12, 3, 0)])
-def test_tensor_core_solve(torch, q, seed, tcg_device):
+@pytest.mark.parametrize("q,seed,tcg_device,lowprec", [(8, 1, 1, 0.0), (12, 3, 1, 0.0),
+                                                       (12, 3, 0, 0.0), (12, 3, 1, 1e-3)])
+def test_tensor_core_solve(torch, q, seed, tcg_device, lowprec):
     inst = instance(q, seed)
     prm = mds.manidsdp_default_params()
     prm.precision_mode = mds.PREC_MIXED
     prm.tensor_cores = 1
     prm.tcg_device = tcg_device
+    prm.tc_lowprec_eta = lowprec
     ctx = mds.manidsdp_setup(inst["N"], inst["m"], inst["idx"], inst["b"], params=prm)
     try:
         rep, _ = mds.manidsdp_solve(ctx, gaussian_factor(inst["N"], 2, seed), 2)
