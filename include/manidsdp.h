@@ -90,7 +90,10 @@ typedef struct {
                              throughout */
   int32_t p0, p_min, p_max, delta_max; /* 1 <= p0 <= p_max <= 512 */
   int32_t max_outer, max_rtr, max_tcg, carry_halvings;
-  int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max */
+  int32_t lanczos_k;      /* Krylov dimension cap for lambda_min / lambda_max (default
+                             2000, at most N); a solve stops, and accepts a rank-one
+                             rounding, only on a Lanczos run whose smallest Ritz pair
+                             converged (residual <= 1e-10 of the spectrum's scale) */
   int32_t precision_mode; /* MANIDSDP_PREC_* */
   int32_t verbose;        /* 1: one line per outer iteration on stderr */
   int32_t profile;        /* 1: time each phase with CUDA events on the context's

@@ -70,7 +70,7 @@ DEFAULTS = dict(
     max_outer=300, max_rtr=15, max_tcg=60, tol=1e-8,
     tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1.0, tcg_floor=1e-10, tcg_abs=0.1,
     rank_tol=1e-6, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0, round_eta=1e-2,
-    lanczos_k=300,
+    lanczos_k=2000,
 )
 
 

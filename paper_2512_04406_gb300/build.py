@@ -21,6 +21,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "kernels_seg.cu", "kernels_dense.cu", "kernels_tcg.cu", "kernels_df64.cu", "kernels_gemm32.cu", "kernels_sddmm.cu", "bqp_setup.cpp", "noalloc.cu", "kernels_tcx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
+# host threads for the p x p tridiagonalisation of the rank update
+OMP = ["-Xcompiler", "-fopenmp"]
 
 
 def _nvcc() -> str:
@@ -38,7 +40,7 @@ def _digest() -> str:
             h.update(f.encode())
             with open(path, "rb") as fh:
                 h.update(fh.read())
-    h.update(" ".join(SOURCES + ARCH + FLAGS).encode())
+    h.update(" ".join(SOURCES + ARCH + FLAGS + OMP).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -57,9 +59,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *OMP, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, *FLAGS, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
+            cmd = [nvcc, *FLAGS, *OMP, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -70,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", *OMP, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -102,6 +102,9 @@ struct manidsdp_ctx {
   float *YTh = nullptr, *YTl = nullptr, *UTh = nullptr, *UTl = nullptr;    // p x ldg
   float* Wfull = nullptr;  // W = Y Up' + Up Y' at every entry (N x ldg)
   int tc_pairs = 1;        // 1: TF32 pairs (three products); 0: single TF32 products
+  double* lz_prev = nullptr;  // the last certificate's lambda_min Ritz vector (N)
+  double* lz_lock = nullptr;  // a vector held out of a Lanczos run (N)
+  bool lz_prev_ok = false;
   int2* tiles = nullptr;  // upper-triangle 128 x 128 tile pairs of the SDDMM
   int ntiles = 0;
   bool resume_have_U = false;  // the last iteration augmented Y = [Y, 0] and set U = [0, V]
@@ -410,12 +413,25 @@ struct LanczosOut {
   std::vector<double> lo;  // smallest Ritz values (ascending), those returned
   double hi = 0.0;
   int steps = 0;
+  // the smallest Ritz pair met the residual test (or the Krylov space became
+  // invariant): lo[0] is lambda_min to rounding; false after k steps without it,
+  // when lo[0] is only an upper bound of lambda_min
+  bool converged = false;
   int nvec = 0;  // Ritz vectors written to c->Vn (N x nvec, row-major)
 };
 
 // Lanczos with full reorthogonalisation on X = XD - Diag(z) (z on device).
+// warm (device N, may be NULL): a previous eigenvector estimate mixed into the
+// start vector (start = warm + 0.1 r, r the fixed splitmix64 vector, normalised),
+// so that a Krylov space of the slightly changed certificate still holds every
+// eigendirection while it starts next to the one sought.
+// lock (device N, unit norm, may be NULL): a known eigenvector kept out of the
+// Krylov space (it sits in front of the basis, so reorthogonalisation removes
+// it), e.g. the exact null vector Yr/sqrt(N) of a rank-one point's certificate;
+// the Ritz values are then those of X on its orthogonal complement.
 LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
-                   bool want_vecs = true) {
+                   bool want_vecs = true, const double* warm = nullptr,
+                   const double* lock = nullptr) {
   const int N = c->N;
   double t_lz = 0.0;
   if (c->prm.profile) {
@@ -434,19 +450,36 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
   }
   nrm = std::sqrt(nrm);
   for (int i = 0; i < N; ++i) v0[i] /= nrm;
-  MDS_CUDA(cudaMemcpyAsync(c->LV, v0.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->s));
+  const int off = lock != nullptr ? 1 : 0;
+  double* KV = c->LV + size_t(off) * N;  // the Krylov vectors
+  if (lock != nullptr)
+    MDS_CUDA(cudaMemcpyAsync(c->LV, lock, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  MDS_CUDA(cudaMemcpyAsync(KV, v0.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->s));
+  if (warm != nullptr) launch_axpby(N, 1.0, warm, 0.1, KV, KV, c->s);
+  if (lock != nullptr) {
+    double d;
+    dots(c, N, 1, c->LV, KV, &d);
+    launch_axpby(N, -d, c->LV, 1.0, KV, KV, c->s);
+  }
+  if (warm != nullptr || lock != nullptr) {
+    double nn;
+    dots(c, N, 1, KV, KV, &nn);
+    launch_axpby(N, 1.0 / std::sqrt(nn), KV, 0.0, nullptr, KV, c->s);
+  }
   std::vector<double> al, be;
   int steps = k;
   double res_lo = 0.0;
+  bool conv = false;
   for (int j = 0; j < k; ++j) {
-    const double* vj = c->LV + size_t(j) * N;
+    const double* vj = KV + size_t(j) * N;
     launch_gemv_cert(N, c->XD, z, vj, c->lw, c->s);
     c->lanczos_mv++;
-    launch_basis_dots(N, j + 1, c->LV, c->lw, c->lh, c->s);
-    MDS_CUDA(cudaMemcpyAsync(c->hp + 8, c->lh + j, sizeof(double), cudaMemcpyDeviceToHost, c->s));
-    launch_basis_update(N, j + 1, c->LV, c->lh, c->lw, c->s);
-    launch_basis_dots(N, j + 1, c->LV, c->lw, c->lh, c->s);
-    launch_basis_update(N, j + 1, c->LV, c->lh, c->lw, c->s);
+    launch_basis_dots(N, off + j + 1, c->LV, c->lw, c->lh, c->s);
+    MDS_CUDA(cudaMemcpyAsync(c->hp + 8, c->lh + off + j, sizeof(double), cudaMemcpyDeviceToHost,
+                             c->s));
+    launch_basis_update(N, off + j + 1, c->LV, c->lh, c->lw, c->s);
+    launch_basis_dots(N, off + j + 1, c->LV, c->lw, c->lh, c->s);
+    launch_basis_update(N, off + j + 1, c->LV, c->lh, c->lw, c->s);
     double bb;
     dots(c, N, 1, c->lw, c->lw, &bb);  // synchronises; hp[8] now holds alpha_j
     const double alpha = c->hp[8];
@@ -454,10 +487,11 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
     al.push_back(alpha);
     if (beta <= 1e-14 * std::max(1.0, std::fabs(alpha)) || j == k - 1) {
       steps = j + 1;
+      conv = beta <= 1e-14 * std::max(1.0, std::fabs(alpha)) || j + 1 == N;
       break;
     }
     be.push_back(beta);
-    launch_axpby(N, 1.0 / beta, c->lw, 0.0, nullptr, c->LV + size_t(j + 1) * N, c->s);
+    launch_axpby(N, 1.0 / beta, c->lw, 0.0, nullptr, KV + size_t(j + 1) * N, c->s);
     // convergence of the extreme Ritz pairs every 10 steps
     if ((j + 1) % 10 == 0) {
       const int kk = j + 1;
@@ -470,12 +504,14 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
       const double res_hi = beta * std::fabs(shi[kk - 1]);
       if (res_lo <= 1e-10 * scale && res_hi <= 1e-6 * scale) {
         steps = kk;
+        conv = true;
         break;
       }
     }
   }
   LanczosOut out;
   out.steps = steps;
+  out.converged = conv;
   const int kk = steps;
   std::vector<double> bt(be.begin(), be.begin() + std::max(0, kk - 1));
   std::vector<double> at(al.begin(), al.begin() + kk);
@@ -493,7 +529,7 @@ LanczosOut lanczos(manidsdp_ctx* c, const double* z, int kcap, int n_small,
     for (int j = 0; j < kk; ++j) neg[j] = -svecs[i][j];
     MDS_CUDA(cudaMemcpyAsync(c->lh, neg.data(), kk * sizeof(double), cudaMemcpyHostToDevice, c->s));
     MDS_CUDA(cudaMemsetAsync(c->lw, 0, N * sizeof(double), c->s));
-    launch_basis_update(N, kk, c->LV, c->lh, c->lw, c->s);
+    launch_basis_update(N, kk, KV, c->lh, c->lw, c->s);
     // sign: first nonzero entry positive
     MDS_CUDA(cudaMemcpyAsync(c->ls, c->lw, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
     std::vector<double> hv(N);
@@ -543,7 +579,7 @@ void default_params(manidsdp_params* p) {
   p->max_rtr = 15;
   p->max_tcg = 60;
   p->carry_halvings = 30;
-  p->lanczos_k = 300;
+  p->lanczos_k = 2000;
   p->precision_mode = MANIDSDP_PREC_FP64;
   p->verbose = 0;
   p->profile = 0;
@@ -822,9 +858,11 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
       c->normC = std::sqrt(cc);
     }
     c->kmax = std::min(std::max(prm.lanczos_k, 1), N);
-    c->LV = dalloc<double>(c, size_t(c->kmax + 1) * N);
-    c->lh = dalloc<double>(c, c->kmax + 1);
+    c->LV = dalloc<double>(c, size_t(c->kmax + 2) * N);  // + a locked vector
+    c->lh = dalloc<double>(c, c->kmax + 2);
     c->lw = dalloc<double>(c, N);
+    c->lz_prev = dalloc<double>(c, N);
+    c->lz_lock = dalloc<double>(c, N);
     c->ls = dalloc<double>(c, N);
     set_state(c, nullptr, prm.sigma0);
     return MANIDSDP_OK;
@@ -1199,6 +1237,7 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
     c->hessvecs = c->rtr_iters = c->lanczos_mv = c->evals = c->grads = 0;
     c->hv_psum = c->ms_hv = c->ms_eval = c->ms_grad = c->ms_lz = c->ms_rank = 0.0;
     const bool resume = P.warm_start && c->resume_valid;
+    if (!resume) c->lz_prev_ok = false;
     int p = p0;
     double rscale = -1.0;
     double sigma = P.sigma0;
@@ -1278,14 +1317,22 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
                           nullptr, c->gws, c->gws_bytes, c->s);
       launch_rowdot(N, p, c->GY, c->Y, c->z, c->s);
       // step 9: extreme eigenpairs of X
-      LanczosOut lo = lanczos(c, c->z, P.lanczos_k, std::max(1, P.delta_max));
+      // the carried negative-curvature directions need converged Ritz vectors,
+      // so the full Krylov cap; warm-started from the previous certificate's vector
+      const int nsmall = std::max(1, P.delta_max);
+      LanczosOut lo = lanczos(c, c->z, P.lanczos_k, nsmall, true,
+                              c->lz_prev_ok ? c->lz_prev : nullptr);
       double by;
       dots(c, c->m, 1, c->b, c->y, &by);
       rep.eta_p = rnorm / (1.0 + c->normC);
-      rep.eta_d = std::max(0.0, -lo.lo[0]) / (1.0 + std::fabs(lo.hi));
       rep.pobj = sum_z + c->xdc;
       rep.value = by;
       rep.eta_g = std::fabs(rep.pobj - by) / (1.0 + std::fabs(rep.pobj) + std::fabs(by));
+      if (lo.nvec > 0) {  // warm start of the next certificate check
+        launch_pad_cols(N, lo.nvec, 1, c->Vn, c->lz_prev, c->s);
+        c->lz_prev_ok = true;
+      }
+      rep.eta_d = std::max(0.0, -lo.lo[0]) / (1.0 + std::fabs(lo.hi));
       rep.lambda_min = lo.lo[0];
       rep.lambda_max = lo.hi;
       rep.sigma = sigma;
@@ -1305,7 +1352,8 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
         status = MANIDSDP_E_NONFINITE;
         break;
       }
-      if (eta <= P.tol) {
+      // the stop needs lambda_min itself, not an upper bound of it
+      if (eta <= P.tol && lo.converged) {
         status = MANIDSDP_OK;
         break;
       }
@@ -1335,14 +1383,19 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
             launch_gemm<double>(N, 1, N, c->XD, N, c->Yt, 1, c->GY, 1, 1.0, 0.0, nullptr, nullptr,
                                 0.0, nullptr, c->gws, c->gws_bytes, c->s);
             launch_rowdot(N, 1, c->GY, c->Yt, c->zt, c->s);
-            LanczosOut lr = lanczos(c, c->zt, P.lanczos_k, 1, false);
+            // Yr / sqrt(N) is an exact null vector of X_r (X_r Yr = 0 entrywise
+            // since Yr_i^2 = 1): lock it, so that Lanczos resolves the rest of
+            // the spectrum instead of a cluster at zero
+            launch_axpby(N, 1.0 / std::sqrt(double(N)), c->Yt, 0.0, nullptr, c->lz_lock, c->s);
+            LanczosOut lr = lanczos(c, c->zt, P.lanczos_k, 1, false,
+                                    c->lz_prev_ok ? c->lz_prev : nullptr, c->lz_lock);
             double byr;
             dots(c, c->m, 1, c->b, c->yt, &byr);
             const double ed = std::max(0.0, -lr.lo[0]) / (1.0 + std::fabs(lr.hi));
             // with R = 0 the evaluated Psi is <Xt + D, S_r + C> = sum(z_r) + <C, Xt + D>
             const double po = fr;
             const double eg = std::fabs(po - byr) / (1.0 + std::fabs(po) + std::fabs(byr));
-            if (std::max(ed, eg) <= P.tol) {
+            if (std::max(ed, eg) <= P.tol && lr.converged) {
               MDS_CUDA(cudaMemcpyAsync(c->Y, c->Yt, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
               MDS_CUDA(cudaMemcpyAsync(c->y, c->yt, c->m * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
               MDS_CUDA(cudaMemcpyAsync(c->z, c->zt, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));

@@ -50,16 +50,20 @@ inline SymTridiag sym_tridiag(std::vector<double> A, int n) {
     t.beta[k] = beta;
     t.e[k] = mu;
     // p = beta A22 v;  w = p - (beta p'v / 2) v;  A22 -= v w' + w v'
-    double pvv = 0.0;
+    // rows are independent in both passes: threads split them (same arithmetic
+    // per entry whatever the thread count, so the result does not depend on it)
+#pragma omp parallel for schedule(static) if (m >= 128)
     for (int i = 0; i < m; ++i) {
       const double* row = &A[size_t(k + 1 + i) * n + k + 1];
       double s = 0.0;
       for (int j = 0; j < m; ++j) s += row[j] * v[j];
       pv[i] = beta * s;
-      pvv += pv[i] * v[i];
     }
+    double pvv = 0.0;
+    for (int i = 0; i < m; ++i) pvv += pv[i] * v[i];
     const double K = 0.5 * beta * pvv;
     for (int i = 0; i < m; ++i) wv[i] = pv[i] - K * v[i];
+#pragma omp parallel for schedule(static) if (m >= 128)
     for (int i = 0; i < m; ++i) {
       double* row = &A[size_t(k + 1 + i) * n + k + 1];
       const double vi = v[i], wi = wv[i];

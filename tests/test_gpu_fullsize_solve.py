@@ -29,7 +29,7 @@ def big():
     return instance(Q80, seed=0)
 
 
-def _solve(big, max_outer, lanczos_k=300):
+def _solve(big, max_outer, lanczos_k=None):
     torch = torch_cuda()
     N, m = big["N"], big["m"]
     p0 = int(np.ceil(np.log(m)))
@@ -37,7 +37,8 @@ def _solve(big, max_outer, lanczos_k=300):
     prm.precision_mode = mds.PREC_MIXED
     prm.tensor_cores = 1
     prm.max_outer = max_outer
-    prm.lanczos_k = lanczos_k
+    if lanczos_k is not None:
+        prm.lanczos_k = lanczos_k
     ctx = mds.manidsdp_setup(N, m, big["idx"], big["b"], params=prm)
     Y0 = gaussian_factor(N, p0, 0)
     Yout = np.empty(N * prm.p_max)
