@@ -169,6 +169,56 @@ int manidsdp_setup(manidsdp_ctx** ctx, int32_t N, int64_t m, const int32_t* idx,
                    const double* b, int32_t c_kind, const double* c_dense,
                    const manidsdp_params* params, void* stream);
 
+/* ---- extended set-up: index layouts, sparse C, the complex relaxation ---- */
+#define MANIDSDP_C_CSR 2        /* C given as a symmetric CSR matrix (both triangles) */
+#define MANIDSDP_IDX_FULL 0     /* idx holds all N x N entries, row-major */
+#define MANIDSDP_IDX_PACKED_UPPER 1 /* idx holds the N(N+1)/2 entries (b <= g), row by row */
+
+typedef struct {
+  int32_t N;              /* order of S (complex: n, the number of unit-modulus variables) */
+  int64_t m;              /* classes (ignored when is_complex) */
+  const int32_t* idx;     /* host, layout idx_layout (ignored when is_complex) */
+  int32_t idx_layout;     /* MANIDSDP_IDX_FULL or MANIDSDP_IDX_PACKED_UPPER */
+  const double* b;        /* host or device, m FP64 (ignored when is_complex) */
+  int32_t c_kind;         /* MANIDSDP_C_ZERO, _DENSE or _CSR */
+  const double* c_dense;  /* DENSE: host or device N x N FP64 */
+  const int64_t* c_rowptr; /* CSR: host N + 1 */
+  const int32_t* c_col;   /* CSR: host nnz column indices (sorted or not, no duplicates) */
+  const double* c_val;    /* CSR: host nnz values; the matrix must be symmetric */
+  int32_t is_complex;     /* 1: the first-order complex relaxation below */
+  const double* q_re;     /* complex: host or device n x n FP64, Re Q (symmetric) */
+  const double* q_im;     /* complex: host or device n x n FP64, Im Q (antisymmetric), or NULL */
+} manidsdp_problem;
+
+/*
+ * manidsdp_setup_ex - manidsdp_setup from a problem descriptor.
+ *   idx_layout = MANIDSDP_IDX_PACKED_UPPER: idx lists the upper triangle (b <= g)
+ *     row by row; the library mirrors it (the classes are symmetric by definition,
+ *     Section 2).
+ *   c_kind = MANIDSDP_C_CSR: C given in CSR form (Section 2, Eq. (DSDP) with a
+ *     sparse cost); it is expanded to the dense N x N operand on the device - the
+ *     multiplier Xt and G = Xt + D - sigma R are dense in any case, so the SpMM
+ *     form would not remove a dense pass.
+ *   is_complex = 1: the first-order relaxation of min z^H Q z over |z_i| = 1,
+ *     min <Q, S> over Hermitian S >= 0 with diag(S) = 1 (the complex counterpart of
+ *     the relaxations of Section 3.1, solved in the factored form of Section 4 on
+ *     the complex oblique manifold).  Every off-diagonal entry is its own class, so
+ *     R = 0 on the manifold and a solve is a rank-adaptive Riemannian trust region
+ *     certified by X = Q - Diag(mu), mu_i = Re (Q Y Y^H)_ii (Proposition 4.2 with
+ *     G = Q; Theorem 4.5).  For such a context, factors Y (n x 2p FP64) hold
+ *     Y = A + iB as [A | B] row-major with p complex columns, and the entry points
+ *     take p as that number of complex columns: manidsdp_subproblem_eval (psi = f,
+ *     rgrad, z = mu; y and rnorm unused), manidsdp_hessvec, manidsdp_lanczos (on the
+ *     real embedding [[Xre, -Xim], [Xim, Xre]], v of length 2n = [Re; Im]) and
+ *     manidsdp_solve (y_out and Xt_out must be NULL; eta_p = 0).  Defaults of the
+ *     complex solve: RTR to ||grad|| <= tol_grad_min (at most 500 iterations), one
+ *     column appended per outer round while lambda_min < -neg_tol (1 + |lambda_max|),
+ *     p <= min(p_max, 256).  The optimal value's sensitivity is dV/dQ = S* = Y Y^H.
+ * Errors as manidsdp_setup (E_ARG for an inconsistent descriptor).
+ */
+int manidsdp_setup_ex(manidsdp_ctx** ctx, const manidsdp_problem* prob,
+                      const manidsdp_params* params, void* stream);
+
 /* Release every resource of the context (NULL is a no-op). */
 void manidsdp_destroy(manidsdp_ctx* ctx);
 

@@ -24,12 +24,14 @@ __all__ = [
     "manidsdp_hessvec", "manidsdp_lanczos", "manidsdp_solve", "manidsdp_bqp_index_map",
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
     "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms", "manidsdp_ucqp_index_map",
-    "manidsdp_ucqp_rhs",
+    "manidsdp_ucqp_rhs", "Problem", "manidsdp_setup_ex", "manidsdp_setup_complex", "C_CSR",
+    "IDX_FULL", "IDX_PACKED_UPPER",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 E_TOOLARGE = -7
-C_ZERO, C_DENSE = 0, 1
+C_ZERO, C_DENSE, C_CSR = 0, 1, 2
+IDX_FULL, IDX_PACKED_UPPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 EIG_MIN, EIG_MAX = 0, 1
 
@@ -77,6 +79,16 @@ class Context(ctypes.c_void_p):
     """Opaque manidsdp_ctx*."""
 
 
+class Problem(ctypes.Structure):
+    """manidsdp_problem (the descriptor of manidsdp_setup_ex)."""
+    _fields_ = [("N", ctypes.c_int32), ("m", ctypes.c_int64), ("idx", ctypes.c_void_p),
+                ("idx_layout", ctypes.c_int32), ("b", ctypes.c_void_p), ("c_kind", ctypes.c_int32),
+                ("c_dense", ctypes.c_void_p), ("c_rowptr", ctypes.c_void_p),
+                ("c_col", ctypes.c_void_p), ("c_val", ctypes.c_void_p),
+                ("is_complex", ctypes.c_int32), ("q_re", ctypes.c_void_p),
+                ("q_im", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _sig = {
@@ -87,6 +99,8 @@ _sig = {
     "manidsdp_setup": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.c_int32, ctypes.c_int64, _P,
                                       _P, ctypes.c_int32, _P, ctypes.POINTER(Params), _P]),
     "manidsdp_destroy": (None, [Context]),
+    "manidsdp_setup_ex": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.POINTER(Problem),
+                                         ctypes.POINTER(Params), _P]),
     "manidsdp_set_state": (ctypes.c_int, [Context, _P, ctypes.c_double]),
     "manidsdp_set_params": (ctypes.c_int, [Context, ctypes.POINTER(Params)]),
     "manidsdp_get_multiplier": (ctypes.c_int, [Context, _P]),
@@ -184,6 +198,34 @@ def manidsdp_setup(N: int, m: int, idx, b, c_kind: int = C_ZERO, c_dense=None,
                              ctypes.byref(params) if params is not None else None, stream)
     _check(st, "manidsdp_setup")
     return ctx
+
+
+def manidsdp_setup_ex(N: int, m: int = 0, idx=None, b=None, idx_layout: int = IDX_FULL,
+                      c_kind: int = C_ZERO, c_dense=None, c_rowptr=None, c_col=None, c_val=None,
+                      is_complex: int = 0, q_re=None, q_im=None, params: Params | None = None,
+                      stream: int | None = None) -> Context:
+    """manidsdp_setup_ex: packed-upper index maps, a CSR cost C, or the first-order
+    complex relaxation (is_complex = 1 with q_re, q_im)."""
+    prob = Problem(N=N, m=m, idx=_ptr(idx, np.int32), idx_layout=idx_layout,
+                   b=_ptr(b, np.float64), c_kind=c_kind, c_dense=_ptr(c_dense, np.float64),
+                   c_rowptr=_ptr(c_rowptr, np.int64), c_col=_ptr(c_col, np.int32),
+                   c_val=_ptr(c_val, np.float64), is_complex=is_complex,
+                   q_re=_ptr(q_re, np.float64), q_im=_ptr(q_im, np.float64))
+    ctx = Context()
+    st = _lib.manidsdp_setup_ex(ctypes.byref(ctx), ctypes.byref(prob),
+                                ctypes.byref(params) if params is not None else None, stream)
+    _check(st, "manidsdp_setup_ex")
+    return ctx
+
+
+def manidsdp_setup_complex(Q, params: Params | None = None, stream: int | None = None) -> Context:
+    """The first-order complex relaxation of min z^H Q z over |z_i| = 1 for a
+    Hermitian (NumPy complex) Q; factors are n x 2p real arrays [Re | Im]."""
+    Q = np.asarray(Q)
+    qre = np.ascontiguousarray(Q.real, dtype=np.float64)
+    qim = np.ascontiguousarray(Q.imag, dtype=np.float64)
+    return manidsdp_setup_ex(Q.shape[0], is_complex=1, q_re=qre, q_im=qim, params=params,
+                             stream=stream)
 
 
 def manidsdp_destroy(ctx: Context) -> None:

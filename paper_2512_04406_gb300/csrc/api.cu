@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "host_linalg.h"
+#include "complex1.h"
 
 using namespace mds;
 using namespace mds::hostla;
@@ -41,6 +42,7 @@ uint64_t splitmix64(uint64_t x) {
 }  // namespace
 
 struct manidsdp_ctx {
+  mds::ComplexState* cx = nullptr;  // the first-order complex relaxation (setup_ex)
   int N = 0;
   int64_t m = 0;
   int c_kind = 0;
@@ -879,11 +881,79 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
 void manidsdp_destroy(manidsdp_ctx* ctx) {
   if (ctx == nullptr) return;
   cudaStreamSynchronize(ctx->s);
+  if (ctx->cx) complex_destroy(ctx->cx);
   release(ctx);
   delete ctx;
 }
 
+int manidsdp_setup_ex(manidsdp_ctx** ctx_out, const manidsdp_problem* pr,
+                      const manidsdp_params* params, void* stream) {
+  if (ctx_out == nullptr || pr == nullptr) return MANIDSDP_E_ARG;
+  manidsdp_params prm;
+  if (params)
+    prm = *params;
+  else
+    default_params(&prm);
+  if (!params_ok(prm)) return MANIDSDP_E_ARG;
+  if (pr->is_complex) {
+    if (pr->N < 1 || 2 * int64_t(pr->N) > kMaxN || pr->q_re == nullptr) return MANIDSDP_E_ARG;
+    auto* c = new (std::nothrow) manidsdp_ctx();
+    if (c == nullptr) return MANIDSDP_E_NOMEM;
+    c->N = pr->N;
+    c->prm = prm;
+    c->s = static_cast<cudaStream_t>(stream);
+    const int st = complex_setup(&c->cx, pr->N, pr->q_re, pr->q_im, prm, c->s);
+    if (st != MANIDSDP_OK) {
+      delete c;
+      return st;
+    }
+    *ctx_out = c;
+    return MANIDSDP_OK;
+  }
+  const int N = pr->N;
+  if (N < 1 || N > kMaxN || pr->idx == nullptr ||
+      (pr->idx_layout != MANIDSDP_IDX_FULL && pr->idx_layout != MANIDSDP_IDX_PACKED_UPPER))
+    return MANIDSDP_E_ARG;
+  const size_t NN = size_t(N) * N;
+  std::vector<int32_t> full;
+  const int32_t* idx = pr->idx;
+  if (pr->idx_layout == MANIDSDP_IDX_PACKED_UPPER) {  // mirror the upper triangle
+    full.resize(NN);
+    size_t e = 0;
+    for (int r = 0; r < N; ++r)
+      for (int g = r; g < N; ++g, ++e) full[size_t(r) * N + g] = full[size_t(g) * N + r] = idx[e];
+    idx = full.data();
+  }
+  std::vector<double> cd;
+  const double* cdense = pr->c_dense;
+  int32_t kind = pr->c_kind;
+  if (kind == MANIDSDP_C_CSR) {  // expand to the dense operand; must be symmetric
+    if (pr->c_rowptr == nullptr || pr->c_rowptr[0] != 0) return MANIDSDP_E_ARG;
+    cd.assign(NN, 0.0);
+    for (int r = 0; r < N; ++r) {
+      if (pr->c_rowptr[r + 1] < pr->c_rowptr[r]) return MANIDSDP_E_ARG;
+      for (int64_t e = pr->c_rowptr[r]; e < pr->c_rowptr[r + 1]; ++e) {
+        const int32_t g = pr->c_col[e];
+        if (g < 0 || g >= N || cd[size_t(r) * N + g] != 0.0) return MANIDSDP_E_ARG;
+        cd[size_t(r) * N + g] = pr->c_val[e];
+      }
+    }
+    for (int r = 0; r < N; ++r)
+      for (int g = r + 1; g < N; ++g)
+        if (cd[size_t(r) * N + g] != cd[size_t(g) * N + r]) return MANIDSDP_E_ARG;
+    cdense = cd.data();
+    kind = MANIDSDP_C_DENSE;
+  }
+  return manidsdp_setup(ctx_out, N, pr->m, idx, pr->b, kind, cdense, &prm, stream);
+}
+
 int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
+  if (c != nullptr && prm != nullptr && c->cx != nullptr) {
+    if (!params_ok(*prm) || prm->precision_mode < 0) return MANIDSDP_E_ARG;
+    const int st = complex_set_params(c->cx, *prm);
+    if (st == MANIDSDP_OK) c->prm = *prm;
+    return st;
+  }
   if (c == nullptr || prm == nullptr || !params_ok(*prm) || prm->p_max != c->prm.p_max ||
       prm->precision_mode != c->prm.precision_mode)
     return MANIDSDP_E_ARG;
@@ -895,6 +965,7 @@ int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
 }
 
 int manidsdp_set_state(manidsdp_ctx* c, const double* Xt, double sigma) {
+  if (c != nullptr && c->cx != nullptr) return MANIDSDP_E_ARG;  // no multiplier (R = 0)
   if (c == nullptr || !(sigma > 0.0)) return MANIDSDP_E_ARG;
   return guard([&]() -> int {
     if (Xt != nullptr) {
@@ -909,6 +980,7 @@ int manidsdp_set_state(manidsdp_ctx* c, const double* Xt, double sigma) {
 }
 
 int manidsdp_get_multiplier(manidsdp_ctx* c, double* Xt) {
+  if (c != nullptr && c->cx != nullptr) return MANIDSDP_E_ARG;  // no multiplier (R = 0)
   if (c == nullptr || Xt == nullptr) return MANIDSDP_E_ARG;
   return guard([&]() -> int {
     const size_t NN = size_t(c->N) * c->N;
@@ -921,6 +993,7 @@ int manidsdp_get_multiplier(manidsdp_ctx* c, double* Xt) {
 }
 
 int manidsdp_get_dual_matrix(manidsdp_ctx* c, double* XD) {
+  if (c != nullptr && c->cx != nullptr) return MANIDSDP_E_ARG;  // no multiplier (R = 0)
   if (c == nullptr || XD == nullptr) return MANIDSDP_E_ARG;
   return guard([&]() -> int {
     const size_t NN = size_t(c->N) * c->N;
@@ -932,6 +1005,11 @@ int manidsdp_get_dual_matrix(manidsdp_ctx* c, double* XD) {
 
 int manidsdp_subproblem_eval(manidsdp_ctx* c, const double* Y, int32_t p, double* psi,
                              double* rgrad, double* z, double* y, double* rnorm) {
+  if (c != nullptr && c->cx != nullptr) {
+    if (Y == nullptr || y != nullptr) return MANIDSDP_E_ARG;
+    if (rnorm) *rnorm = 0.0;
+    return complex_eval(c->cx, Y, p, psi, rgrad, z);
+  }
   if (c == nullptr || Y == nullptr || p < 1 || p > c->pcap) return MANIDSDP_E_ARG;
   return guard([&]() -> int {
     const size_t np = size_t(c->N) * p;
@@ -960,6 +1038,10 @@ int manidsdp_subproblem_eval(manidsdp_ctx* c, const double* Y, int32_t p, double
 
 int manidsdp_hessvec(manidsdp_ctx* c, const double* Y, const double* U, int32_t p, double* HU,
                      int32_t precision) {
+  if (c != nullptr && c->cx != nullptr) {
+    if (Y == nullptr || U == nullptr || HU == nullptr) return MANIDSDP_E_ARG;
+    return complex_hessvec(c->cx, Y, U, p, HU, precision);
+  }
   if (c == nullptr || Y == nullptr || U == nullptr || HU == nullptr || p < 1 || p > c->pcap ||
       (precision != MANIDSDP_PREC_FP64 && precision != MANIDSDP_PREC_MIXED))
     return MANIDSDP_E_ARG;
@@ -976,6 +1058,12 @@ int manidsdp_hessvec(manidsdp_ctx* c, const double* Y, const double* U, int32_t 
 
 int manidsdp_lanczos(manidsdp_ctx* c, const double* Y, int32_t p, int32_t which, int32_t k,
                      double* lambda, double* v, int32_t* steps) {
+  if (c != nullptr && c->cx != nullptr) {
+    if (Y == nullptr || lambda == nullptr || (which != MANIDSDP_EIG_MIN && which != MANIDSDP_EIG_MAX))
+      return MANIDSDP_E_ARG;
+    return complex_lanczos(c->cx, Y, p, which, k, lambda, which == MANIDSDP_EIG_MIN ? v : nullptr,
+                           steps);
+  }
   if (c == nullptr || Y == nullptr || p < 1 || p > c->pcap || lambda == nullptr ||
       (which != MANIDSDP_EIG_MIN && which != MANIDSDP_EIG_MAX))
     return MANIDSDP_E_ARG;
@@ -1227,6 +1315,10 @@ void relayout(manidsdp_ctx* c, double* buf, int p_old, int p_new) {
 extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, double* Y_out,
                               int32_t* p_out, double* y_out, double* z_out, double* Xt_out,
                               manidsdp_report* report) {
+  if (c != nullptr && c->cx != nullptr) {
+    if (y_out != nullptr || Xt_out != nullptr) return MANIDSDP_E_ARG;
+    return complex_solve(c->cx, Y0, p0, Y_out, p_out, z_out, report);
+  }
   if (c == nullptr || Y0 == nullptr || p0 < 1 || p0 > c->pcap) return MANIDSDP_E_ARG;
   int status = MANIDSDP_E_NOCONV;
   manidsdp_report rep{};

@@ -409,7 +409,8 @@ __device__ __forceinline__ void x_split(float x, float& hi, float& lo) {
 }
 
 // X (N x p FP64, leading dimension p) as TF32 pairs, row-major (leading dimension
-// ld) and, when hiT is given, transposed (p x N, leading dimension ldt).
+// ld; skipped when hi is null) and, when hiT is given, transposed (p x N, leading
+// dimension ldt).
 __global__ void __launch_bounds__(256) x_split_rows_kernel(int N, int p, const double* __restrict__ X,
                                                            float* __restrict__ hi,
                                                            float* __restrict__ lo, int ld,
@@ -423,8 +424,10 @@ __global__ void __launch_bounds__(256) x_split_rows_kernel(int N, int p, const d
     float h = 0.f, l = 0.f;
     if (r < N && c < p) {
       x_split(float(X[size_t(r) * p + c]), h, l);
-      hi[size_t(r) * ld + c] = h;
-      lo[size_t(r) * ld + c] = l;
+      if (hi != nullptr) {
+        hi[size_t(r) * ld + c] = h;
+        lo[size_t(r) * ld + c] = l;
+      }
     }
     th[i][tx] = h;
     tl[i][tx] = l;
