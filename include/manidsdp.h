@@ -404,6 +404,75 @@ int manidsdp_sparse_bqp_index_map(int32_t q, int32_t t, int32_t* N, int64_t* m,
  * symmetric); cs: host t x q or NULL. */
 int manidsdp_sparse_bqp_rhs(int32_t q, int32_t t, const double* Qs, const double* cs, double* b);
 
+/* ---- batched solve: many small instances in one persistent launch --------- */
+
+/* Per-instance result of a batched solve (KKT residuals of Section 6). */
+typedef struct {
+  double value;                /* b'y, the relaxation value */
+  double eta_p, eta_d, eta_g;  /* KKT residuals at the returned point */
+  double lambda_min;           /* smallest eigenvalue of the certificate X */
+  int32_t status;              /* MANIDSDP_OK, E_NOCONV or E_NONFINITE */
+  int32_t p;                   /* final factor width (1 after an accepted rounding) */
+  int32_t outer, hessvecs;     /* outer iterations, Hessian-vector products */
+} manidsdp_batch_out;
+
+typedef struct manidsdp_batch manidsdp_batch; /* opaque, owned by the library */
+
+/*
+ * manidsdp_batch_setup - prepare ninst independent instances of (DSDP) with
+ * C = 0 and index-map operators (as manidsdp_setup), each solved by Algorithm 1
+ * in the same readings as manidsdp_solve, for one persistent kernel launch in
+ * which every CTA takes whole instances from a device-side counter and runs the
+ * outer loop, RTR/tCG, the multiplier update, the certificate's eigenpairs (a
+ * parallel Jacobi method: the certificate is the full N x N X, computed exactly
+ * rather than by Lanczos), the rank update, the sigma rule (5.1), the rank-one
+ * rounding and the carried negative-curvature direction (Theorem 4.5) on the
+ * device, with no host round trip.
+ *   N[i] in [1, 128]; m[i] in [1, N[i]^2]: host arrays of length ninst.
+ *   idx: host, the ninst full N[i] x N[i] index maps concatenated (row-major,
+ *        symmetric, every class in [0, m[i]) nonempty).
+ *   b:   host, the ninst right-hand sides concatenated (sum m[i] FP64).
+ *   params: NULL for the defaults with p_max = 32; p_max <= 32; precision_mode
+ *        MANIDSDP_PREC_MIXED (FP32 Hessian-vector products) or _FP64 (all FP64);
+ *        lanczos_k, tcg_device, tensor_cores, warm_start, profile, verbose and
+ *        tc_lowprec_eta are ignored.
+ * Every starting factor is N[i] x p0.  Errors: E_ARG (as manidsdp_setup, or a size
+ * above the limits), E_NONFINITE (b), E_NOMEM, E_CUDA.  The launch shape is the
+ * one tuned earlier in the process for the same (max N, p_max, precision), else
+ * 256 threads per CTA at the occupancy limit.
+ */
+int manidsdp_batch_setup(manidsdp_batch** batch, int32_t ninst, const int32_t* N,
+                         const int64_t* m, const int32_t* idx, const double* b,
+                         const manidsdp_params* params, void* stream);
+
+/* Solve every instance from the starting factors Y0 (host or device: the N[i] x p0
+ * factors concatenated; rows are normalised on the device).  res: host array of
+ * ninst results or NULL; y: host or device, the optimal multipliers y_i (sum m[i]
+ * FP64, concatenated; dV_i/db_i = y_i) or NULL; ms: device time of the launch or
+ * NULL.  Returns MANIDSDP_OK when every instance met eta_max <= tol, E_NONFINITE if
+ * one met a non-finite value, E_NOCONV if one reached max_outer (res tells which),
+ * E_CUDA. */
+int manidsdp_batch_solve(manidsdp_batch* batch, const double* Y0, manidsdp_batch_out* res,
+                         double* y, float* ms);
+
+/* Launch-shape tuner: solves the batch once for each shape (128 or 256 threads per
+ * CTA; 1, 2, 4, ... CTAs per SM up to the occupancy limit), keeps the fastest for
+ * this batch and records it for later batches with the same (max N, p_max,
+ * precision).  threads, ctas_per_sm: host outputs or NULL. */
+int manidsdp_batch_tune(manidsdp_batch* batch, const double* Y0, int32_t* threads,
+                        int32_t* ctas_per_sm);
+
+/* Fix the launch shape: threads in {128, 256}; ctas_per_sm 0 = the occupancy limit. */
+int manidsdp_batch_set_launch(manidsdp_batch* batch, int32_t threads, int32_t ctas_per_sm);
+
+/* Release the batch (NULL is a no-op). */
+void manidsdp_batch_destroy(manidsdp_batch* batch);
+
+/* One call: manidsdp_batch_setup, manidsdp_batch_solve, manidsdp_batch_destroy. */
+int manidsdp_solve_batched(int32_t ninst, const int32_t* N, const int64_t* m, const int32_t* idx,
+                           const double* b, const double* Y0, const manidsdp_params* params,
+                           manidsdp_batch_out* res, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

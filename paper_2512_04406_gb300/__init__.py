@@ -25,7 +25,9 @@ __all__ = [
     "manidsdp_bqp_rhs", "PREC_FP64", "PREC_MIXED", "EIG_MIN", "EIG_MAX", "C_ZERO", "C_DENSE",
     "lib_path", "manidsdp_launch_count", "manidsdp_hessvec_stage_ms", "manidsdp_ucqp_index_map",
     "manidsdp_ucqp_rhs", "Problem", "manidsdp_setup_ex", "manidsdp_setup_complex", "C_CSR",
-    "IDX_FULL", "IDX_PACKED_UPPER",
+    "IDX_FULL", "IDX_PACKED_UPPER", "BatchOut", "Batch", "manidsdp_batch_setup",
+    "manidsdp_batch_solve", "manidsdp_batch_tune", "manidsdp_batch_set_launch",
+    "manidsdp_batch_destroy", "manidsdp_solve_batched",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -89,6 +91,22 @@ class Problem(ctypes.Structure):
                 ("q_im", ctypes.c_void_p)]
 
 
+class BatchOut(ctypes.Structure):
+    """manidsdp_batch_out: one instance's result of a batched solve."""
+    _fields_ = [("value", ctypes.c_double), ("eta_p", ctypes.c_double),
+                ("eta_d", ctypes.c_double), ("eta_g", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("status", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("outer", ctypes.c_int32), ("hessvecs", ctypes.c_int32)]
+
+    @property
+    def eta_max(self):
+        return max(self.eta_p, self.eta_d, self.eta_g)
+
+
+class Batch(ctypes.c_void_p):
+    """Opaque manidsdp_batch*."""
+
+
 _P = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _sig = {
@@ -129,6 +147,15 @@ _sig = {
                                                       ctypes.c_int32,
                                                       ctypes.POINTER(ctypes.c_double), _P,
                                                       ctypes.POINTER(ctypes.c_int32), _P]),
+    "manidsdp_batch_setup": (ctypes.c_int, [ctypes.POINTER(Batch), ctypes.c_int32, _P, _P, _P, _P,
+                                            ctypes.POINTER(Params), _P]),
+    "manidsdp_batch_solve": (ctypes.c_int, [Batch, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "manidsdp_batch_tune": (ctypes.c_int, [Batch, _P, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "manidsdp_batch_set_launch": (ctypes.c_int, [Batch, ctypes.c_int32, ctypes.c_int32]),
+    "manidsdp_batch_destroy": (None, [Batch]),
+    "manidsdp_solve_batched": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P,
+                                              ctypes.POINTER(Params), _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -390,3 +417,80 @@ def manidsdp_ucqp_rhs(q: int, Q, c=None) -> np.ndarray:
     _check(_lib.manidsdp_ucqp_rhs(q, _ptr(Q), _ptr(c), _ptr(b, np.float64, True)),
            "manidsdp_ucqp_rhs")
     return b
+
+
+def _batch_arrays(Ns, ms, idx, b):
+    """Concatenated host arrays of a batch: (ninst, N int32, m int64, idx int32, b FP64).
+    idx and b are lists of per-instance arrays or already-concatenated arrays."""
+    Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+    ms = np.ascontiguousarray(ms, dtype=np.int64)
+    if len(Ns) != len(ms):
+        raise ValueError("N and m must have one entry per instance")
+    if isinstance(idx, (list, tuple)):
+        idx = np.concatenate([np.asarray(a, dtype=np.int32).ravel() for a in idx])
+    if isinstance(b, (list, tuple)):
+        b = np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in b])
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if idx.size != int((Ns.astype(np.int64) ** 2).sum()) or b.size != int(ms.sum()):
+        raise ValueError("idx must hold sum N_i^2 entries and b sum m_i entries")
+    return len(Ns), Ns, ms, idx, b
+
+
+def manidsdp_batch_setup(Ns, ms, idx, b, params: Params | None = None,
+                         stream: int | None = None) -> Batch:
+    """manidsdp_batch_setup over per-instance index maps idx[i] (N_i x N_i) and
+    right-hand sides b[i] (m_i); lists or concatenated arrays.  The arrays are
+    kept alive on the returned handle (the library copies them at setup)."""
+    n, Ns, ms, idx, b = _batch_arrays(Ns, ms, idx, b)
+    bt = Batch()
+    st = _lib.manidsdp_batch_setup(ctypes.byref(bt), n, _ptr(Ns), _ptr(ms), _ptr(idx), _ptr(b),
+                                   ctypes.byref(params) if params is not None else None, stream)
+    _check(st, "manidsdp_batch_setup")
+    bt._meta = (n, Ns, ms)
+    return bt
+
+
+def _y0_len(bt: Batch, p0: int) -> int:
+    return int(bt._meta[1].astype(np.int64).sum()) * p0
+
+
+def manidsdp_batch_solve(bt: Batch, Y0, y=None, raise_on_noconv: bool = False):
+    """Returns (list of BatchOut, device ms).  Y0: the N_i x p0 starting factors
+    concatenated (host array or CUDA tensor).  y: optional output of sum m_i FP64."""
+    n = bt._meta[0]
+    res = (BatchOut * n)()
+    ms = ctypes.c_float()
+    st = _lib.manidsdp_batch_solve(bt, _ptr(Y0, np.float64), ctypes.cast(res, _P),
+                                   _ptr(y, np.float64, True), ctypes.byref(ms))
+    _check(st, "manidsdp_batch_solve", allow=(OK,) if raise_on_noconv else (OK, E_NOCONV))
+    return list(res), ms.value
+
+
+def manidsdp_batch_tune(bt: Batch, Y0):
+    """Returns the chosen (threads per CTA, CTAs per SM)."""
+    th, per = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.manidsdp_batch_tune(bt, _ptr(Y0, np.float64), ctypes.byref(th),
+                                    ctypes.byref(per)), "manidsdp_batch_tune")
+    return th.value, per.value
+
+
+def manidsdp_batch_set_launch(bt: Batch, threads: int, ctas_per_sm: int = 0) -> None:
+    _check(_lib.manidsdp_batch_set_launch(bt, threads, ctas_per_sm), "manidsdp_batch_set_launch")
+
+
+def manidsdp_batch_destroy(bt: Batch) -> None:
+    _lib.manidsdp_batch_destroy(bt)
+
+
+def manidsdp_solve_batched(Ns, ms, idx, b, Y0, params: Params | None = None, y=None,
+                           stream: int | None = None, raise_on_noconv: bool = False):
+    """One call (setup, solve, destroy).  Returns the list of BatchOut."""
+    n, Ns, ms, idx, b = _batch_arrays(Ns, ms, idx, b)
+    res = (BatchOut * n)()
+    st = _lib.manidsdp_solve_batched(n, _ptr(Ns), _ptr(ms), _ptr(idx), _ptr(b),
+                                     _ptr(Y0, np.float64),
+                                     ctypes.byref(params) if params is not None else None,
+                                     ctypes.cast(res, _P), _ptr(y, np.float64, True), stream)
+    _check(st, "manidsdp_solve_batched", allow=(OK,) if raise_on_noconv else (OK, E_NOCONV))
+    return list(res)

@@ -160,3 +160,38 @@ def test_sparse_bqp_index_map_and_rhs_bit_exact_vs_oracle(q, t):
     assert np.array_equal(mds.manidsdp_sparse_bqp_rhs(q, t, Qs, cs), mb.rhs(q, t, Qs, cs))
     assert np.array_equal(mds.manidsdp_sparse_bqp_rhs(q, t, Qs, None),
                           mb.rhs(q, t, Qs, [np.zeros(q)] * t))
+
+
+def test_batch_setup_rejects_bad_instances_before_touching_the_gpu():
+    """The batched entry points validate every instance on the host first."""
+    N1, m1, idx1 = mds.manidsdp_bqp_index_map(4, 2)
+    N2, m2, idx2 = mds.manidsdp_bqp_index_map(20, 1)
+    good = ([N1, N2], [m1, m2], [idx1, idx2], [np.zeros(m1), np.zeros(m2)])
+    bad_sym = idx2.copy(); bad_sym[0, 1] = (bad_sym[0, 1] + 1) % m2
+    cases = [
+        ([N1, N2], [m1, m2], [idx1, bad_sym], good[3]),                 # not symmetric
+        ([N1, N2], [m1, m2 + 1], [idx1, idx2], [np.zeros(m1), np.zeros(m2 + 1)]),  # empty class
+    ]
+    for Ns, ms, idx, b in cases:
+        with pytest.raises(mds.ManidsdpError) as e:
+            mds.manidsdp_batch_setup(Ns, ms, idx, b)
+        assert e.value.status == mds.E_ARG
+    # N above the one-CTA limit of 128: the order-2 moment matrix at q = 15 has N = 121,
+    # at q = 16 N = 137
+    N3, m3, idx3 = mds.manidsdp_bqp_index_map(16, 2)
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_batch_setup([N3], [m3], [idx3], [np.zeros(m3)])
+    assert e.value.status == mds.E_ARG
+    for field, value in (("p_max", 33), ("p0", 0), ("precision_mode", 4), ("gamma", 0.5)):
+        prm = mds.manidsdp_default_params()
+        prm.p_max = 32
+        setattr(prm, field, value)
+        with pytest.raises(mds.ManidsdpError) as e:
+            mds.manidsdp_batch_setup(*good, params=prm)
+        assert e.value.status == mds.E_ARG
+    with pytest.raises(ValueError):  # sizes inconsistent with the arrays
+        mds.manidsdp_batch_setup([N1], [m1], [idx1, idx2], [np.zeros(m1)])
+    b_nan = np.zeros(m1); b_nan[0] = np.nan
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_batch_setup([N1], [m1], [idx1], [b_nan])
+    assert e.value.status == mds.E_NONFINITE
