@@ -414,6 +414,11 @@ typedef struct {
   int32_t status;              /* MANIDSDP_OK, E_NOCONV or E_NONFINITE */
   int32_t p;                   /* final factor width (1 after an accepted rounding) */
   int32_t outer, hessvecs;     /* outer iterations, Hessian-vector products */
+  int64_t cycles[5];           /* params.profile = 1: SM clock cycles of the instance's
+                                  CTA spent in the whole solve, the Hessian-vector
+                                  products, the certificate's eigenpairs, the
+                                  subproblem evaluations and the eigenpairs of Y'Y
+                                  (0 otherwise) */
 } manidsdp_batch_out;
 
 typedef struct manidsdp_batch manidsdp_batch; /* opaque, owned by the library */
@@ -434,8 +439,8 @@ typedef struct manidsdp_batch manidsdp_batch; /* opaque, owned by the library */
  *   b:   host, the ninst right-hand sides concatenated (sum m[i] FP64).
  *   params: NULL for the defaults with p_max = 32; p_max <= 32; precision_mode
  *        MANIDSDP_PREC_MIXED (FP32 Hessian-vector products) or _FP64 (all FP64);
- *        lanczos_k, tcg_device, tensor_cores, warm_start, profile, verbose and
- *        tc_lowprec_eta are ignored.
+ *        profile = 1 fills manidsdp_batch_out.cycles; lanczos_k, tcg_device,
+ *        tensor_cores, warm_start, verbose and tc_lowprec_eta are ignored.
  * Every starting factor is N[i] x p0.  Errors: E_ARG (as manidsdp_setup, or a size
  * above the limits), E_NONFINITE (b), E_NOMEM, E_CUDA.  The launch shape is the
  * one tuned earlier in the process for the same (max N, p_max, precision), else
@@ -455,14 +460,14 @@ int manidsdp_batch_setup(manidsdp_batch** batch, int32_t ninst, const int32_t* N
 int manidsdp_batch_solve(manidsdp_batch* batch, const double* Y0, manidsdp_batch_out* res,
                          double* y, float* ms);
 
-/* Launch-shape tuner: solves the batch once for each shape (128 or 256 threads per
- * CTA; 1, 2, 4, ... CTAs per SM up to the occupancy limit), keeps the fastest for
+/* Launch-shape tuner: solves the batch once for each shape (128, 256 or 512 threads
+ * per CTA; 1, 2, 4, ... CTAs per SM up to the occupancy limit), keeps the fastest for
  * this batch and records it for later batches with the same (max N, p_max,
  * precision).  threads, ctas_per_sm: host outputs or NULL. */
 int manidsdp_batch_tune(manidsdp_batch* batch, const double* Y0, int32_t* threads,
                         int32_t* ctas_per_sm);
 
-/* Fix the launch shape: threads in {128, 256}; ctas_per_sm 0 = the occupancy limit. */
+/* Fix the launch shape: threads in {128, 256, 512}; ctas_per_sm 0 = the occupancy limit. */
 int manidsdp_batch_set_launch(manidsdp_batch* batch, int32_t threads, int32_t ctas_per_sm);
 
 /* Release the batch (NULL is a no-op). */

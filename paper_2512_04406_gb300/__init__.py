@@ -96,7 +96,8 @@ class BatchOut(ctypes.Structure):
     _fields_ = [("value", ctypes.c_double), ("eta_p", ctypes.c_double),
                 ("eta_d", ctypes.c_double), ("eta_g", ctypes.c_double),
                 ("lambda_min", ctypes.c_double), ("status", ctypes.c_int32),
-                ("p", ctypes.c_int32), ("outer", ctypes.c_int32), ("hessvecs", ctypes.c_int32)]
+                ("p", ctypes.c_int32), ("outer", ctypes.c_int32), ("hessvecs", ctypes.c_int32),
+                ("cycles", ctypes.c_int64 * 5)]
 
     @property
     def eta_max(self):

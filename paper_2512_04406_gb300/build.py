@@ -18,7 +18,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmanidsdp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "kernels_seg.cu", "kernels_dense.cu", "kernels_tcg.cu", "kernels_df64.cu", "kernels_gemm32.cu", "kernels_sddmm.cu", "bqp_setup.cpp", "noalloc.cu", "kernels_tcx.cu", "complex1.cu", "batched.cu"]
+SOURCES = ["api.cu", "kernels_seg.cu", "kernels_dense.cu", "kernels_tcg.cu", "kernels_df64.cu", "kernels_gemm32.cu", "kernels_sddmm.cu", "bqp_setup.cpp", "noalloc.cu", "kernels_tcx.cu", "complex1.cu", "batched.cu", "batched_k128.cu", "batched_k256.cu", "batched_k512.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 # host threads for the p x p tridiagonalisation of the rank update

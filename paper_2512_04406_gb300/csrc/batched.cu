@@ -1,106 +1,42 @@
-// Thousands of small instances in one persistent launch (manidsdp_batch_*).
+// Thousands of small instances in one persistent launch (manidsdp_batch_*):
+// the host side (validation, packing, launch, tuner).
 //
-// Every CTA takes instances from a global counter (dynamic scheduling, so
-// instances of uneven size balance across the SMs) and runs the whole of
-// Algorithm 1 on each, with the readings of the single-instance path and its
-// oracle: RTR with truncated CG on the ALM subproblem (Section 4, Proposition
-// 4.2), the multiplier update and certificate (Algorithm 1 steps 4-9), the rank
-// update, the sigma rule (5.1), the rank-one rounding, the carried
-// negative-curvature direction (Theorem 4.5).  Every decision is taken on the
-// device; the host only packs the instances and reads the results.
+// Every CTA takes instances from a global counter, longest first (instances
+// sorted by decreasing N, so the long ones do not finish last), and runs the
+// whole of Algorithm 1 on each with the readings of the single-instance path and
+// its oracle: RTR with truncated CG on the ALM subproblem (Section 4,
+// Proposition 4.2), the multiplier update and certificate (Algorithm 1 steps
+// 4-9), the rank update, the sigma rule (5.1), the rank-one rounding and the
+// carried negative-curvature direction (Theorem 4.5).  Every decision is taken
+// on the device; the host packs the instances and reads the results.
 //
-// Sizes: N <= 128 (moment matrices of the order-1 relaxations with n <= 127 and
-// of the order-2 ones with n <= 14), factor width p <= 32.  The cost, gradient,
-// multiplier and certificate are FP64; the tCG Hessian-vector products are FP32
-// (W = Y Up' + Up Y' and Q(W) = W - A*(w) entrywise, T = G Up + sigma Q(W) Y).
-// The certificate's eigenpairs (and those of the p x p Gram Y'Y of the rank
-// update) come from a parallel two-sided Jacobi method in FP64: n/2 disjoint
-// rotations per step in round-robin order, rows then columns, until the
-// off-diagonal mass is below 1e-30 of the total.
+// Sizes: N <= 128 (moment matrices of the first-order relaxations with
+// n <= 127 and of the second-order ones with n <= 14), factor width p <= 32.
+// Cost, gradient, multiplier update and certificate are FP64; the tCG
+// Hessian-vector products are FP32 from shared memory (MANIDSDP_PREC_MIXED) or
+// FP64 (MANIDSDP_PREC_FP64).  The certificate's eigen-information comes from a
+// Householder tridiagonalisation, Sturm-count multisection and inverse
+// iteration (batched_dev.cuh).
 //
-// Per-CTA workspace in global memory (reused across the CTA's instances, L1/L2
-// resident at these sizes).  Instance data: the N x N index map, per-class lists
-// of the upper-triangle entries (class-sum order fixed, so results are
-// deterministic), multiplicities and b.
+// Instance data, packed into one device buffer: the N x N class map (int32 and
+// uint16), per-class lists of the upper-triangle entries split into pieces of
+// at most kBPiece entries (class sums in a fixed order, so results do not
+// depend on the launch shape), multiplicities, b and 1/mult.  Per-CTA
+// workspace in global memory, reused across the CTA's instances.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <functional>
 #include <map>
 #include <mutex>
-#include <tuple>
 #include <new>
+#include <tuple>
 #include <vector>
 
-#include "common.cuh"
+#include "batched.cuh"
 
 namespace mds {
-namespace {
-
-constexpr int kBMaxN = 128;
-constexpr int kBMaxP = 32;
-
-struct BInst {
-  int N, m;
-  long long off_idx;   // N*N int32 (class of each entry)
-  long long off_cptr;  // m+1 int32: entries of class a at cent[cptr[a] .. cptr[a+1])
-  long long off_cent;  // upper-triangle entries r*N + c (r <= c), int32
-  long long off_cls;   // m doubles: mult, then b (2m)
-  long long off_y0;    // element offset of the N x p0 starting factor in Y0
-};
-
-struct BParams {
-  double sigma0, sigma_min, sigma_max, gamma, kappa1, kappa2, tol;
-  double tol_grad_min, tol_grad_max, tol_grad_factor, rank_tol, neg_tol, tcg_floor, tcg_abs;
-  double carry_t0, round_eta;
-  int p0, p_min, p_max, delta_max, max_outer, max_rtr, max_tcg, carry_halvings;
-  int fp64;  // 1: FP64 Hessian-vector products (MANIDSDP_PREC_FP64)
-};
-
-struct BOut {  // per instance
-  double value, eta_p, eta_d, eta_g, lambda_min;
-  int status, p, outer, hessvecs;
-};
-
-// Per-CTA workspace offsets (doubles), for Nmax, mmax.
-struct BLayout {
-  long long XD, G, E, EV, W32, G32;             // N*N (W32, G32 floats in double slots)
-  long long Y, Yt, grad, eta, Heta, r, dlt, Hd, Up, U, GY, T;  // N*P
-  long long y, yt, w;                            // m
-  long long z, zt, ev, tmpN;                     // N
-  long long gram, gev, gvec;                     // P*P
-  long long total;
-};
-
-__host__ __device__ inline BLayout make_layout(int N, int m) {
-  BLayout L;
-  long long o = 0;
-  const long long nn = (long long)N * N, np = (long long)N * kBMaxP, pp = kBMaxP * kBMaxP;
-  L.XD = o; o += nn; L.G = o; o += nn; L.E = o; o += nn; L.EV = o; o += nn;
-  L.W32 = o; o += (nn + 1) / 2; L.G32 = o; o += (nn + 1) / 2;
-  L.Y = o; o += np; L.Yt = o; o += np; L.grad = o; o += np; L.eta = o; o += np;
-  L.Heta = o; o += np; L.r = o; o += np; L.dlt = o; o += np; L.Hd = o; o += np;
-  L.Up = o; o += np; L.U = o; o += np; L.GY = o; o += np; L.T = o; o += np;
-  L.y = o; o += m; L.yt = o; o += m; L.w = o; o += m;
-  L.z = o; o += N; L.zt = o; o += N; L.ev = o; o += N; L.tmpN = o; o += N;
-  L.gram = o; o += pp; L.gev = o; o += kBMaxP; L.gvec = o; o += pp;
-  L.total = o;
-  return L;
-}
-
-// The device code for each CTA size the tuner chooses from.
-namespace bt128 {
-constexpr int kBT = 128;
-#include "batched_dev.cuh"
-}  // namespace bt128
-namespace bt256 {
-constexpr int kBT = 256;
-#include "batched_dev.cuh"
-}  // namespace bt256
-
-}  // namespace
-
-// ---- host side --------------------------------------------------------------
+namespace batch {
 namespace {
 
 BParams to_bparams(const manidsdp_params& p) {
@@ -113,16 +49,24 @@ BParams to_bparams(const manidsdp_params& p) {
   b.delta_max = p.delta_max; b.max_outer = p.max_outer; b.max_rtr = p.max_rtr;
   b.max_tcg = p.max_tcg; b.carry_halvings = p.carry_halvings;
   b.fp64 = p.precision_mode == MANIDSDP_PREC_FP64 ? 1 : 0;
+  b.profile = p.profile ? 1 : 0;
   return b;
 }
 
 size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
-using KernelFn = void (*)(int, const BInst*, const char*, const double*, BParams, double*, long long,
-                          int, int, int*, BOut*, double*, const long long*);
-
 KernelFn kernel_for(int threads) {
-  return threads == 128 ? bt128::batched_solve_kernel : bt256::batched_solve_kernel;
+  return threads == 128 ? bt128::kernel() : threads == 256 ? bt256::kernel() : bt512::kernel();
+}
+
+unsigned smem_bytes(int threads, int N, int m, int np, int P4) {
+  return threads == 128   ? bt128::smem_bytes(N, m, np, P4)
+         : threads == 256 ? bt256::smem_bytes(N, m, np, P4)
+                          : bt512::smem_bytes(N, m, np, P4);
+}
+
+constexpr int kShapes[3] = {128, 256, 512};  // threads per CTA the tuner tries
+int shape_index(int threads) { return threads == 128 ? 0 : threads == 256 ? 1 : 2;
 }
 
 // Tuned launch shapes, shared by every batch of the process: key (N_max, p_max,
@@ -131,6 +75,7 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
 
 }  // namespace
+}  // namespace batch
 }  // namespace mds
 
 struct manidsdp_batch {
@@ -138,28 +83,31 @@ struct manidsdp_batch {
   long long y0_len = 0, y_len = 0;
   cudaStream_t s = nullptr;
   manidsdp_params prm{};
-  mds::BParams P{};
+  mds::batch::BParams P{};
   char* data = nullptr;        // packed instance data (device)
-  mds::BInst* inst = nullptr;  // device
+  mds::batch::BInst* inst = nullptr;  // device
+  int* order = nullptr;        // device: instances by decreasing size (longest first)
+  unsigned smem[3] = {0, 0, 0};  // dynamic shared memory at 128, 256 and 512 threads
   long long* y_off = nullptr;  // device
   double* y0 = nullptr;        // device, concatenated starting factors
   double* y_out = nullptr;     // device, concatenated multipliers
-  mds::BOut* out = nullptr;    // device
+  mds::batch::BOut* out = nullptr;    // device
   int* next = nullptr;         // device counter
   double* ws = nullptr;        // per-CTA workspaces
   long long ws_stride = 0;
   int ws_ctas = 0;             // CTAs the workspace holds
   int threads = 256, per_sm = 0;
-  int occ[2] = {1, 1};         // occupancy limit at 128 and 256 threads
+  int occ[3] = {1, 1, 1};      // occupancy limit at 128, 256 and 512 threads
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
 namespace {
 
 using namespace mds;
+using namespace mds::batch;
 
 void batch_release(manidsdp_batch* b) {
-  void* ptrs[] = {b->data, b->inst, b->y_off, b->y0, b->y_out, b->out, b->next, b->ws};
+  void* ptrs[] = {b->data, b->inst, b->order, b->y_off, b->y0, b->y_out, b->out, b->next, b->ws};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->e0) cudaEventDestroy(b->e0);
@@ -168,7 +116,7 @@ void batch_release(manidsdp_batch* b) {
 }
 
 int batch_grid(const manidsdp_batch* b) {
-  const int occ = b->occ[b->threads == 128 ? 0 : 1];
+  const int occ = b->occ[shape_index(b->threads)];
   const int per_sm = b->per_sm > 0 ? std::min(b->per_sm, occ) : occ;
   return std::max(1, std::min({b->ninst, b->sms * per_sm, b->ws_ctas}));
 }
@@ -178,9 +126,9 @@ int batch_launch(manidsdp_batch* b, float* ms) {
   MDS_CUDA(cudaMemsetAsync(b->next, 0, sizeof(int), b->s));
   MDS_CUDA(cudaEventRecord(b->e0, b->s));
   count_launches(1);
-  kernel_for(b->threads)<<<batch_grid(b), b->threads, 0, b->s>>>(
-      b->ninst, b->inst, b->data, b->y0, b->P, b->ws, b->ws_stride, b->nmax, b->mmax, b->next,
-      b->out, b->y_out, b->y_off);
+  kernel_for(b->threads)<<<batch_grid(b), b->threads, b->smem[shape_index(b->threads)], b->s>>>(
+      b->ninst, b->inst, b->order, b->data, b->y0, b->P, b->ws, b->ws_stride, b->nmax, b->mmax,
+      b->next, b->out, b->y_out, b->y_off);
   MDS_CUDA(cudaGetLastError());
   MDS_CUDA(cudaEventRecord(b->e1, b->s));
   MDS_CUDA(cudaEventSynchronize(b->e1));
@@ -240,6 +188,8 @@ int manidsdp_batch_setup(manidsdp_batch** out, int32_t ninst, const int32_t* Ns,
     return (long long)off;
   };
   int nmax = 0, mmax = 0;
+  unsigned smem_need[3] = {0, 0, 0};
+  const int P4 = (prm.p_max + 3) & ~3;
   long long yo = 0, y0o = 0;
   size_t io = 0, bo = 0;
   for (int i = 0; i < ninst; ++i) {
@@ -263,29 +213,61 @@ int manidsdp_batch_setup(manidsdp_batch** out, int32_t ninst, const int32_t* Ns,
       if (!std::isfinite(bb[a])) return MANIDSDP_E_NONFINITE;
       cptr[a + 1] += cptr[a];
     }
-    std::vector<int32_t> cent(cptr[m]);
+    std::vector<uint32_t> cent(cptr[m]);
     std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
     for (int r = 0; r < N; ++r)
-      for (int c = r; c < N; ++c) cent[fill[idx[size_t(r) * N + c]]++] = r * N + c;
-    std::vector<double> cls(2 * m);
+      for (int c = r; c < N; ++c) cent[fill[idx[size_t(r) * N + c]]++] = (uint32_t(r) << 16) | uint32_t(c);
+    std::vector<double> cls(3 * m);
+    std::vector<float> invmf(m);
     for (int64_t a = 0; a < m; ++a) {
       cls[a] = double(cnt[a]);
       cls[m + a] = bb[a];
+      cls[2 * m + a] = 1.0 / double(cnt[a]);
+      invmf[a] = float(1.0 / double(cnt[a]));
     }
     BInst& I = insts[i];
     I.N = N;
     I.m = int(m);
     I.off_idx = put(idx, size_t(N) * N * 4);
+    {
+      std::vector<uint16_t> i16(size_t(N) * N);
+      for (size_t t = 0; t < i16.size(); ++t) i16[t] = uint16_t(idx[t]);
+      I.off_idx16 = put(i16.data(), i16.size() * 2);
+    }
     I.off_cptr = put(cptr.data(), cptr.size() * 4);
     I.off_cent = put(cent.data(), cent.size() * 4);
     I.off_cls = put(cls.data(), cls.size() * 8);
+    I.off_invmf = put(invmf.data(), invmf.size() * 4);
+    // pieces of at most kBPiece entries, so that no thread sums a long class alone
+    std::vector<int32_t> pstart, pcls, cpc(m + 1, 0);
+    for (int64_t a = 0; a < m; ++a) {
+      cpc[a] = int32_t(pstart.size());
+      for (int32_t e = cptr[a]; e < cptr[a + 1]; e += kBPiece) {
+        pstart.push_back(e);
+        pcls.push_back(int32_t(a));
+      }
+    }
+    cpc[m] = int32_t(pstart.size());
+    pstart.push_back(cptr[m]);
+    I.np = int(pcls.size());
+    I.off_pstart = put(pstart.data(), pstart.size() * 4);
+    I.off_pcls = put(pcls.data(), pcls.size() * 4);
+    I.off_cpc = put(cpc.data(), cpc.size() * 4);
     I.off_y0 = y0o;
     y0o += (long long)N * prm.p0;
     y_off[i] = yo;
     yo += m;
     nmax = std::max(nmax, N);
     mmax = std::max(mmax, int(m));
+    if (prm.precision_mode == MANIDSDP_PREC_MIXED)
+      for (int t = 0; t < 3; ++t) smem_need[t] = std::max(smem_need[t], smem_bytes(kShapes[t], N, int(m), I.np, P4));
   }
+  // longest first: instances by decreasing N (then decreasing m), ties by number
+  std::vector<int> order(ninst);
+  for (int i = 0; i < ninst; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return insts[a].N != insts[c].N ? insts[a].N > insts[c].N : insts[a].m > insts[c].m;
+  });
   auto* b = new (std::nothrow) manidsdp_batch();
   if (b == nullptr) return MANIDSDP_E_NOMEM;
   b->ninst = ninst;
@@ -300,16 +282,27 @@ int manidsdp_batch_setup(manidsdp_batch** out, int32_t ninst, const int32_t* Ns,
     int dev = 0;
     MDS_CUDA(cudaGetDevice(&dev));
     MDS_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
-    MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[0], kernel_for(128), 128, 0));
-    MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[1], kernel_for(256), 256, 0));
-    b->occ[0] = std::max(1, b->occ[0]);
-    b->occ[1] = std::max(1, b->occ[1]);
+    int smem_max = 0;
+    MDS_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (int t = 0; t < 3; ++t) {
+      b->smem[t] = smem_need[t];
+      if (int(smem_need[t]) > smem_max) throw std::bad_alloc();
+      MDS_CUDA(cudaFuncSetAttribute(kernel_for(kShapes[t]), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(smem_need[t])));
+    }
+    for (int t = 0; t < 3; ++t) {
+      MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ[t], kernel_for(kShapes[t]), kShapes[t],
+                                                             b->smem[t]));
+      b->occ[t] = std::max(1, b->occ[t]);
+    }
     MDS_CUDA(cudaEventCreate(&b->e0));
     MDS_CUDA(cudaEventCreate(&b->e1));
     MDS_CUDA(cudaMalloc(&b->data, std::max<size_t>(host.size(), 16)));
     MDS_CUDA(cudaMemcpyAsync(b->data, host.data(), host.size(), cudaMemcpyHostToDevice, b->s));
     MDS_CUDA(cudaMalloc(&b->inst, ninst * sizeof(BInst)));
     MDS_CUDA(cudaMemcpyAsync(b->inst, insts.data(), ninst * sizeof(BInst), cudaMemcpyHostToDevice, b->s));
+    MDS_CUDA(cudaMalloc(&b->order, ninst * sizeof(int)));
+    MDS_CUDA(cudaMemcpyAsync(b->order, order.data(), ninst * sizeof(int), cudaMemcpyHostToDevice, b->s));
     MDS_CUDA(cudaMalloc(&b->y_off, ninst * sizeof(long long)));
     MDS_CUDA(cudaMemcpyAsync(b->y_off, y_off.data(), ninst * sizeof(long long), cudaMemcpyHostToDevice, b->s));
     MDS_CUDA(cudaMalloc(&b->y0, size_t(b->y0_len) * sizeof(double)));
@@ -317,7 +310,7 @@ int manidsdp_batch_setup(manidsdp_batch** out, int32_t ninst, const int32_t* Ns,
     MDS_CUDA(cudaMalloc(&b->out, ninst * sizeof(BOut)));
     MDS_CUDA(cudaMalloc(&b->next, sizeof(int)));
     // workspace for the largest grid any launch shape may use
-    b->ws_ctas = std::min(ninst, b->sms * std::max(b->occ[0], b->occ[1]));
+    b->ws_ctas = std::min(ninst, b->sms * std::max({b->occ[0], b->occ[1], b->occ[2]}));
     b->ws_stride = make_layout(nmax, mmax).total;
     MDS_CUDA(cudaMalloc(&b->ws, size_t(b->ws_ctas) * b->ws_stride * sizeof(double)));
     MDS_CUDA(cudaStreamSynchronize(b->s));
@@ -373,8 +366,8 @@ int manidsdp_batch_tune(manidsdp_batch* b, const double* Y0, int32_t* threads, i
     MDS_CUDA(cudaMemcpyAsync(b->y0, Y0, size_t(b->y0_len) * sizeof(double), cudaMemcpyDefault, b->s));
     float best = INFINITY;
     int bt = b->threads, bs = b->per_sm;
-    for (int th : {128, 256}) {
-      const int occ = b->occ[th == 128 ? 0 : 1];
+    for (int th : kShapes) {
+      const int occ = b->occ[shape_index(th)];
       for (int k = 1; k <= occ; k *= 2) {
         const int per = (k * 2 > occ && k < occ) ? occ : k;  // the last step is the limit itself
         b->threads = th;
@@ -402,7 +395,8 @@ int manidsdp_batch_tune(manidsdp_batch* b, const double* Y0, int32_t* threads, i
 }
 
 int manidsdp_batch_set_launch(manidsdp_batch* b, int32_t threads, int32_t ctas_per_sm) {
-  if (b == nullptr || (threads != 128 && threads != 256) || ctas_per_sm < 0) return MANIDSDP_E_ARG;
+  if (b == nullptr || (threads != 128 && threads != 256 && threads != 512) || ctas_per_sm < 0)
+    return MANIDSDP_E_ARG;
   b->threads = threads;
   b->per_sm = ctas_per_sm;
   return MANIDSDP_OK;
