@@ -24,6 +24,11 @@ takes minutes), the Hess-vec's rate against the tensor pipe (`roofline`), an
 end-to-end solve through the C ABI from pinned host buffers (`e2e`) and the FP64
 oracle timed on the host cores (`cpu_baseline`).
 
+The `batched` object times the batched persistent solver on its own workload:
+4096 independent BQP relaxations (3072 first-order with n in [16, 64], 1024
+second-order with n in [6, 14]) solved to KKT <= 1e-8 in one launch, in
+solves/s, against the per-context FP64 form on a sample (--no-batched skips it).
+
 Under torchrun (N > 1) each rank solves its own replica (the single-instance
 path has no exchange step); value = max-over-ranks time / (K x ranks).
 
@@ -90,6 +95,9 @@ def parse():
                          "(same kernels; for profilers that list kernels one launch at a time)")
     ap.add_argument("--hv-only", type=int, default=0,
                     help="only time the Hessian-vector product at this p (profiling)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-solver line (4096 small relaxations in one launch)")
+    ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--hv-stages", action="store_true",
                     help="with --hv-only: per-stage CUDA events (params.profile = 2, which "
                          "serialises the side stream) and the mean time of each stage")
@@ -316,6 +324,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_mix():
+    """The batch of independent BQP relaxations: 3072 first-order with n uniform on
+    [16, 64] and 1024 second-order with n uniform on [6, 14] (Q, c iid N(0, 1),
+    instance i seeded 1000 + i; starting factors N_i x 2 Gaussian, same seeds),
+    built by the library's host helpers."""
+    import paper_2512_04406_gb300 as mds
+    from synthetic import batched_bqp_sizes, bqp_instance, gaussian_factor
+    s1, s2 = batched_bqp_sizes(3072, 1024, 16, 64, 6, 14)
+    spec = [(int(n), 1) for n in s1] + [(int(n), 2) for n in s2]
+    maps = {}
+    Ns, ms, idxs, bs, ys = [], [], [], [], []
+    for i, (q, order) in enumerate(spec):
+        if (q, order) not in maps:
+            maps[(q, order)] = mds.manidsdp_bqp_index_map(q, order)
+        N, m, idx = maps[(q, order)]
+        Q, c = bqp_instance(q, 1000 + i)
+        Ns.append(N); ms.append(m); idxs.append(idx)
+        bs.append(mds.manidsdp_bqp_rhs(q, Q, c, order))
+        ys.append(gaussian_factor(N, 2, 1000 + i).ravel())
+    return spec, Ns, ms, idxs, bs, np.concatenate(ys)
+
+
+def run_batched(mds, torch, steps, stream):
+    """The batched persistent solver on the 4096-instance mix: solves/s at
+    KKT <= 1e-8 (device time of the launch), after the launch-shape tuner, with
+    an end-to-end figure (host starting factors in, host results out) and the
+    per-context FP64 form (manidsdp_solve per instance) on a strided sample."""
+    spec, Ns, ms, idxs, bs, Y0 = batched_mix()
+    prm = mds.manidsdp_default_params()
+    prm.p_max = 32
+    prm.precision_mode = mds.PREC_MIXED
+    bt = mds.manidsdp_batch_setup(Ns, ms, idxs, bs, prm, stream=stream.cuda_stream)
+    Y0d = torch.tensor(Y0, device="cuda")
+    shape = mds.manidsdp_batch_tune(bt, Y0d)
+    t_dev, res = [], None
+    for _ in range(steps):
+        res, t = mds.manidsdp_batch_solve(bt, Y0d)
+        t_dev.append(t)
+    # end to end: host starting factors in, host results and multipliers out
+    Y0h = torch.from_numpy(Y0).pin_memory()
+    y_h = torch.empty(int(sum(ms)), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mds.manidsdp_batch_solve(bt, Y0h, y_h)
+    t_e2e = time.perf_counter() - t0
+    mds.manidsdp_batch_destroy(bt)
+    n = len(spec)
+    ms_dev = statistics.median(t_dev)
+    # per-context FP64 form on a strided sample (one context per instance)
+    sample = list(range(0, n, 128))
+    t_ctx = 0.0
+    ok_ctx = True
+    for i in sample:
+        pc = mds.manidsdp_default_params()
+        pc.p_max = 32
+        pc.precision_mode = mds.PREC_FP64
+        off = sum(Ns[j] * 2 for j in range(i))
+        t0 = time.perf_counter()
+        cx = mds.manidsdp_setup(Ns[i], ms[i], idxs[i], bs[i], params=pc, stream=stream.cuda_stream)
+        rc, _ = mds.manidsdp_solve(cx, Y0[off:off + Ns[i] * 2], 2)
+        mds.manidsdp_destroy(cx)
+        t_ctx += time.perf_counter() - t0
+        ok_ctx &= rc.status == mds.OK
+    ctx_rate = len(sample) / t_ctx
+    return {
+        "workload": "4096 independent BQP relaxations in one persistent launch: 3072 order-1 "
+                    "(n uniform in [16, 64]) and 1024 order-2 (n uniform in [6, 14]), Q, c iid "
+                    "N(0,1), instance i seeded 1000 + i",
+        "metric": "solves/s at KKT<=1e-8", "value": n / (ms_dev * 1e-3), "unit": "solves/s",
+        "ms_per_batch": ms_dev, "ms_steps": t_dev, "precision": "mixed (FP32 Hess-vec, FP64 rest)",
+        "launch": {"threads": shape[0], "ctas_per_sm": shape[1], "tuned": True},
+        "all_converged": all(r.status == mds.OK and r.eta_max <= 1e-8 for r in res),
+        "max_eta": max(r.eta_max for r in res),
+        "max_outer": max(r.outer for r in res), "hessvecs_total": int(sum(r.hessvecs for r in res)),
+        "e2e": {"value": n / t_e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": int(Y0.nbytes), "d2h_bytes_per_step": int(n * 96 + y_h.numel() * 8),
+                "includes": "H2D of the starting factors, the launch, D2H of the per-instance "
+                            "results and the multipliers y (dV/db)"},
+        "per_context_fp64": {"value": ctx_rate, "unit": "solves/s", "sample": len(sample),
+                             "converged": ok_ctx,
+                             "how": "manidsdp_setup + manidsdp_solve (FP64 form) + destroy per "
+                                    "instance, every 128th instance, wall clock"},
+        "speedup_vs_per_context_fp64": (n / (ms_dev * 1e-3)) / ctx_rate,
+    }
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -493,6 +587,10 @@ def main():
         compare["value_rel_diff"] = abs(compare["fp64"]["value"] - compare["mixed"]["value"]) / abs(
             compare["fp64"]["value"])
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched(mds, torch, args.batched_steps, stream)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         counts = dict(hessvecs=hv_count / len(reps), evals=sum(r.evals for r in reps) / len(reps),
@@ -524,6 +622,7 @@ def main():
                 "rank_update_host": sum(r.ms_rank for r in reps) / len(reps)},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
             "mixed_vs_fp64": compare,
+            "batched": batched,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
