@@ -98,6 +98,12 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-solver line (4096 small relaxations in one launch)")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched solver (profiling)")
+    ap.add_argument("--batched-uniform", type=str, default="",
+                    help="with --batched-only: 'n,count' -- count second-order relaxations at this n "
+                         "(seeds 5000 + i) in place of the 4096-instance mix, 256 threads per CTA, "
+                         "one launch, no tuner")
     ap.add_argument("--hv-stages", action="store_true",
                     help="with --hv-only: per-stage CUDA events (params.profile = 2, which "
                          "serialises the side stream) and the mean time of each stage")
@@ -346,6 +352,30 @@ def batched_mix():
     return spec, Ns, ms, idxs, bs, np.concatenate(ys)
 
 
+def run_batched_uniform(mds, torch, spec, stream):
+    """One launch over `count` second-order relaxations at size n (a profiling case)."""
+    from synthetic import bqp_instance, gaussian_factor
+    n, count = (int(v) for v in spec.split(","))
+    N, m, idx = mds.manidsdp_bqp_index_map(n, 2)
+    bs, ys = [], []
+    for i in range(count):
+        Q, c = bqp_instance(n, 5000 + i)
+        bs.append(mds.manidsdp_bqp_rhs(n, Q, c, 2))
+        ys.append(gaussian_factor(N, 2, 5000 + i).ravel())
+    prm = mds.manidsdp_default_params()
+    prm.p_max = 32
+    prm.precision_mode = mds.PREC_MIXED
+    bt = mds.manidsdp_batch_setup([N] * count, [m] * count, [idx] * count, bs, prm,
+                                  stream=stream.cuda_stream)
+    mds.manidsdp_batch_set_launch(bt, 256, 0)
+    res, ms = mds.manidsdp_batch_solve(bt, np.concatenate(ys))
+    mds.manidsdp_batch_destroy(bt)
+    return {"batched_uniform": True, "n": n, "N": N, "count": count, "ms": ms,
+            "all_converged": all(r.status == mds.OK for r in res),
+            "hessvecs_mean": float(np.mean([r.hessvecs for r in res])),
+            "hessvecs_max": int(max(r.hessvecs for r in res))}
+
+
 def run_batched(mds, torch, steps, stream):
     """The batched persistent solver on the 4096-instance mix: solves/s at
     KKT <= 1e-8 (device time of the launch), after the launch-shape tuner, with
@@ -441,6 +471,13 @@ def main():
     rank, world, local = dist_env()
     assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
     torch.cuda.set_device(local)
+    if args.batched_only:
+        stream = torch.cuda.current_stream()
+        out = (run_batched_uniform(mds, torch, args.batched_uniform, stream) if args.batched_uniform
+               else run_batched(mds, torch, args.batched_steps, stream))
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
