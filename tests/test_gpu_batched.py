@@ -10,7 +10,9 @@ Algorithm 1 on whole instances, against the FP64 oracle.
 - the full mix at the default tolerance: every instance eta_max <= 1e-8;
 - results independent of the grid (each instance is solved by one CTA, so the
   arithmetic does not depend on the number of CTAs), and the tuner's choice valid;
-- the one-call manidsdp_solve_batched agrees with setup + solve.
+- the one-call manidsdp_solve_batched agrees with setup + solve;
+- the batched backward: dV/dQ by central differences on 64 entries (129 solves in
+  one launch) against 2 y[x_i x_j] from the returned multipliers.
 """
 import numpy as np
 import pytest
@@ -137,3 +139,46 @@ def test_batched_grid_independent_and_tuner(sample):
                                      sample["Y0cat"], params(mds.PREC_MIXED))
     # the setup inside the one call picks up the shape just tuned
     assert [r.value for r in one] == [r.value for r in c]
+
+
+@pytest.mark.parametrize("density,seed", [(0.05, 5), (None, 3)])
+def test_batched_dV_dQ_central_differences_64_entries(density, seed):
+    """dV/dQ_ij by central differences, h = 1e-6, on 64 random upper-triangle entries
+    of a q = 12 instance (the sparse-Q recipe at 5 % support, and a dense Q): the
+    129 solves (base and 2 x 64 perturbed) in one batched launch.  Since
+    b[x_i x_j] = Q_ij + Q_ji, the envelope theorem gives dV/dQ_ij (symmetric
+    perturbation E_ij + E_ji) = 2 y[x_i x_j] of the base solve; both instances are
+    tight (rank-one rounding accepted), where the closed form 2 x_i x_j of the
+    optimal vertex also holds."""
+    from synthetic import bqp_instance, gaussian_factor
+    torch_cuda()
+    q, h = 12, 1e-6
+    Q, c = bqp_instance(q, seed, density)
+    N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
+    rng = np.random.default_rng(11)
+    upper = [(i, j) for i in range(q) for j in range(i + 1, q)]
+    pairs = [upper[k] for k in rng.choice(len(upper), 64, replace=False)]
+    Qs = [Q]
+    for i, j in pairs:
+        for s in (1.0, -1.0):
+            Qp = Q.copy()
+            Qp[i, j] += s * h
+            Qp[j, i] += s * h
+            Qs.append(Qp)
+    bs = [mds.manidsdp_bqp_rhs(q, Qk, c, 2) for Qk in Qs]
+    Y0 = np.concatenate([gaussian_factor(N, 2, seed).ravel()] * len(Qs))
+    prm = params(mds.PREC_FP64, tol=1e-12)
+    bt = mds.manidsdp_batch_setup([N] * len(Qs), [m] * len(Qs), [idx] * len(Qs), bs, prm)
+    try:
+        y = np.empty(m * len(Qs))
+        res, _ = mds.manidsdp_batch_solve(bt, Y0, y)
+    finally:
+        mds.manidsdp_batch_destroy(bt)
+    assert all(r.status == mds.OK for r in res)
+    assert all(r.p == 1 for r in res)  # every solve ended on an accepted rounding
+    y0 = y[:m]
+    for t, (i, j) in enumerate(pairs):
+        fd = (res[1 + 2 * t].value - res[2 + 2 * t].value) / (2 * h)
+        k = 1 + q + sum(q - 1 - u for u in range(i)) + (j - i - 1)  # class of x_i x_j
+        assert abs(fd - 2 * y0[k]) <= 1e-5 * max(1.0, abs(fd)), (i, j, fd, 2 * y0[k])
+        assert abs(abs(2 * y0[k]) - 2.0) <= 1e-9  # = 2 x_i x_j at the optimal vertex
