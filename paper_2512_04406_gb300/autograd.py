@@ -90,26 +90,34 @@ class Subproblem:
 
 
 class SDPValue(torch.autograd.Function):
-    """V = value of (DSDP) for the right-hand side b (and C = 0): forward solves
-    with Algorithm 1; backward returns gout * y* (envelope theorem)."""
+    """V = value of (DSDP) for the right-hand side b and a dense symmetric cost C
+    (None: C = 0): forward solves with Algorithm 1; backward returns gout * y*
+    for b and gout * (Xt* + D) for C (envelope theorem on (PSDP))."""
 
     @staticmethod
-    def forward(fctx, b, N, m, idx, Y0, params):
+    def forward(fctx, b, C, N, m, idx, Y0, params):
+        from . import C_DENSE, C_ZERO
         bh = b.detach().cpu().numpy().astype(np.float64)
-        ctx = manidsdp_setup(N, m, idx, bh, params=params)
+        ch = None if C is None else np.ascontiguousarray(C.detach().cpu().numpy(), dtype=np.float64)
+        ctx = manidsdp_setup(N, m, idx, bh, C_DENSE if ch is not None else C_ZERO, ch,
+                             params=params)
         try:
             y = np.empty(m)
             rep, _ = manidsdp_solve(ctx, Y0, Y0.shape[1], y_out=y)
+            XD = np.empty((N, N))
+            manidsdp_get_dual_matrix(ctx, XD)
         finally:
             manidsdp_destroy(ctx)
-        fctx.save_for_backward(torch.tensor(y, dtype=b.dtype, device=b.device))
+        fctx.save_for_backward(torch.tensor(y, dtype=b.dtype, device=b.device),
+                               torch.tensor(XD, dtype=b.dtype, device=b.device))
+        fctx.has_C = C is not None
         fctx.report = rep
         return torch.tensor(rep.value, dtype=b.dtype, device=b.device)
 
     @staticmethod
     def backward(fctx, gout):
-        (y,) = fctx.saved_tensors
-        return gout * y, None, None, None, None, None
+        y, XD = fctx.saved_tensors
+        return gout * y, (gout * XD if fctx.has_C else None), None, None, None, None, None
 
 
 def value_and_sensitivities(N, m, idx, b, Y0, params=None):

@@ -130,3 +130,33 @@ def test_value_sensitivity_dV_dC_matches_dual_matrix():
         mds.manidsdp_destroy(ctx)
     assert r.eta_max <= 1e-8
     assert (r.value - rep.value) / h == pytest.approx(float(b @ e), rel=1e-5, abs=1e-5)
+
+
+def test_sdp_value_backward_gives_y_and_dual_matrix():
+    """SDPValue's backward through torch.autograd: b.grad = y* and C.grad = Xt* + D
+    (the same solve's multiplier and dual matrix), and <C.grad, A*(e)> = b'e for
+    any e (the range(A*) identity of the dV/dC test above)."""
+    torch = torch_cuda()
+    from paper_2512_04406_gb300.autograd import SDPValue, value_and_sensitivities
+    q, seed = 6, 2
+    Q, c = bqp_instance(q, seed)
+    N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
+    b = mds.manidsdp_bqp_rhs(q, Q, c, 2)
+    prm = mds.manidsdp_default_params(); prm.tol = 1e-10; prm.max_outer = 60
+    Y0 = gaussian_factor(N, 2, seed)
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    Ct = torch.zeros((N, N), dtype=torch.float64, device="cuda", requires_grad=True)
+    V = SDPValue.apply(bt, Ct, N, m, idx, Y0, prm)
+    V.backward()
+    rep, y, XD = value_and_sensitivities(N, m, idx, b, Y0, prm)
+    # (a zero dense C takes the dense-C kernels: the same solve up to rounding)
+    assert abs(V.item() - rep.value) <= 1e-10 * abs(rep.value)
+    assert np.abs(bt.grad.cpu().numpy() - y).max() <= 1e-9
+    assert np.abs(Ct.grad.cpu().numpy() - XD).max() <= 1e-9 * (1 + np.abs(XD).max())
+    e = np.random.default_rng(4).standard_normal(m)
+    assert float(np.sum(Ct.grad.cpu().numpy() * e[idx])) == pytest.approx(float(b @ e), rel=1e-9,
+                                                                          abs=1e-9)
+    # C = None: only b gets a gradient
+    bt2 = torch.tensor(b, device="cuda", requires_grad=True)
+    SDPValue.apply(bt2, None, N, m, idx, Y0, prm).backward()
+    assert np.abs(bt2.grad.cpu().numpy() - y).max() <= 1e-12  # the same path as value_and_sensitivities
