@@ -104,6 +104,10 @@ def parse():
                     help="with --batched-only: 'n,count' -- count second-order relaxations at this n "
                          "(seeds 5000 + i) in place of the 4096-instance mix, 256 threads per CTA, "
                          "one launch, no tuner")
+    ap.add_argument("--formulation-curve", type=str, default="",
+                    help="comma-separated q values: solve each dense BQP relaxation with the "
+                         "projected (DSDP') and the direct (DSDP) formulation and print one JSON "
+                         "line per q (the paper's DSDP'-versus-DSDP comparison)")
     ap.add_argument("--hv-stages", action="store_true",
                     help="with --hv-only: per-stage CUDA events (params.profile = 2, which "
                          "serialises the side stream) and the mean time of each stage")
@@ -360,6 +364,34 @@ def batched_mix():
     return spec, Ns, ms, idxs, bs, np.concatenate(ys)
 
 
+def run_formulation_curve(mds, torch, qs, engine, stream):
+    """Solve time to eta_max <= 1e-8 of the q-variable dense BQP relaxation in the
+    projected formulation (DSDP', Algorithm 1) and the direct one (two-block ADMM
+    on DSDP, fixed penalty sigma = 0.25), mixed form, one solve each after a
+    warm-up solve; CUDA events on the library's stream."""
+    from synthetic import gaussian_factor
+    for q in qs:
+        Q, c, N, m, idx, b, p0 = workload(q, 0)
+        Y0 = torch.tensor(gaussian_factor(N, p0, 0), device="cuda")
+        row = {"formulation_curve": True, "q": q, "N": N, "m": m}
+        for name, dflag in (("projected", 0), ("direct", 1)):
+            prm = mds.manidsdp_default_params()
+            prm.precision_mode = mds.PREC_MIXED
+            prm.tensor_cores = 1 if engine == "tc" else 0
+            prm.direct = dflag
+            if dflag:
+                prm.sigma0, prm.kappa1, prm.kappa2, prm.max_outer = 0.25, -1.0, 1e300, 1000
+            ctx = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
+            solve_once(mds, torch, ctx, Y0, p0, stream)  # warm-up (graphs, allocations)
+            rep, p, ms = solve_once(mds, torch, ctx, Y0, p0, stream)
+            mds.manidsdp_destroy(ctx)
+            row[name] = {"s": ms / 1e3, "outer": rep.outer, "hessvecs": rep.hessvecs,
+                         "eta_max": rep.eta_max, "value": rep.value,
+                         "converged": rep.status == mds.OK}
+        row["speedup_projected_over_direct"] = row["direct"]["s"] / row["projected"]["s"]
+        print(json.dumps(row), flush=True)
+
+
 def run_batched_uniform(mds, torch, spec, stream):
     """One launch over `count` second-order relaxations at size n (a profiling case)."""
     from synthetic import bqp_instance, gaussian_factor
@@ -479,6 +511,10 @@ def main():
     rank, world, local = dist_env()
     assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
     torch.cuda.set_device(local)
+    if args.formulation_curve:
+        run_formulation_curve(mds, torch, [int(v) for v in args.formulation_curve.split(",")],
+                              args.engine, torch.cuda.current_stream())
+        return
     if args.batched_only:
         stream = torch.cuda.current_stream()
         out = (run_batched_uniform(mds, torch, args.batched_uniform, stream) if args.batched_uniform

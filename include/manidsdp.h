@@ -113,6 +113,15 @@ typedef struct {
                              relative at N = 3241-7261 against 2-5e-6 for the FP32
                              FMA kernel; same speed at small p, faster at p <= 80
                              for N ~ 3000.  0 (default): FP32 FMA kernel */
+  int32_t direct;         /* 1: the direct two-block ADMM on (DSDP) itself (Section 3, the
+                             comparison with the direct subproblem, Eq.
+                             (direct-ALM-subproblem)): each subproblem keeps y frozen at the
+                             previous outer iteration's y(S) instead of the best response
+                             y(S), so G = Xt + D - sigma (A*(y_k) - S - C) and the Hessian
+                             loses the class-mean term (Eq. (hessian-comparison): sigma I in
+                             place of sigma Q); the multiplier update is unchanged.  0
+                             (default): the variable-projected (DSDP') of Algorithm 1.
+                             manidsdp_solve only (not the batched or complex paths) */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */
@@ -230,6 +239,13 @@ int manidsdp_set_params(manidsdp_ctx* ctx, const manidsdp_params* params);
 /* Replace the ALM state: multiplier Xt (host or device N x N FP64, NULL = zero)
  * and penalty sigma.  Section 3, Algorithm 0. */
 int manidsdp_set_state(manidsdp_ctx* ctx, const double* Xt, double sigma);
+
+/* Direct formulation (params.direct = 1): set the frozen y_k of the subproblem
+ * (host or device, m FP64), the y of Eq. (direct-ALM-subproblem) that
+ * manidsdp_subproblem_eval and manidsdp_hessvec then use in place of y(S).
+ * manidsdp_solve sets it itself (y(S0 + C) at the start, then each outer
+ * iteration's y).  E_ARG for a complex context. */
+int manidsdp_set_direct_y(manidsdp_ctx* ctx, const double* y);
 
 /* Copy out the multiplier Xt (host or device N x N FP64). */
 int manidsdp_get_multiplier(manidsdp_ctx* ctx, double* Xt);

@@ -27,7 +27,7 @@ __all__ = [
     "manidsdp_ucqp_rhs", "Problem", "manidsdp_setup_ex", "manidsdp_setup_complex", "C_CSR",
     "IDX_FULL", "IDX_PACKED_UPPER", "BatchOut", "Batch", "manidsdp_batch_setup",
     "manidsdp_batch_solve", "manidsdp_batch_tune", "manidsdp_batch_set_launch",
-    "manidsdp_batch_destroy", "manidsdp_solve_batched",
+    "manidsdp_batch_destroy", "manidsdp_solve_batched", "manidsdp_set_direct_y",
 ]
 
 OK, E_ARG, E_NONFINITE, E_NOCONV, E_TIMEOUT, E_CUDA, E_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
             "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile", "tcg_device",
-            "warm_start", "tensor_cores")]
+            "warm_start", "tensor_cores", "direct")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -121,6 +121,7 @@ _sig = {
     "manidsdp_setup_ex": (ctypes.c_int, [ctypes.POINTER(Context), ctypes.POINTER(Problem),
                                          ctypes.POINTER(Params), _P]),
     "manidsdp_set_state": (ctypes.c_int, [Context, _P, ctypes.c_double]),
+    "manidsdp_set_direct_y": (ctypes.c_int, [Context, _P]),
     "manidsdp_set_params": (ctypes.c_int, [Context, ctypes.POINTER(Params)]),
     "manidsdp_get_multiplier": (ctypes.c_int, [Context, _P]),
     "manidsdp_get_dual_matrix": (ctypes.c_int, [Context, _P]),
@@ -266,6 +267,10 @@ def manidsdp_set_params(ctx: Context, params: Params) -> None:
 
 def manidsdp_set_state(ctx: Context, Xt=None, sigma: float = 1.0) -> None:
     _check(_lib.manidsdp_set_state(ctx, _ptr(Xt, np.float64), sigma), "manidsdp_set_state")
+
+
+def manidsdp_set_direct_y(ctx: Context, y) -> None:
+    _check(_lib.manidsdp_set_direct_y(ctx, _ptr(y, np.float64)), "manidsdp_set_direct_y")
 
 
 def manidsdp_get_multiplier(ctx: Context, Xt) -> None:

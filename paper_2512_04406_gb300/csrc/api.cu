@@ -62,6 +62,7 @@ struct manidsdp_ctx {
   float *Yh = nullptr, *Yl = nullptr;
   // per class; slot[r*N + c] (r <= c): position of entry (r, c) in the inverse map
   double *y = nullptr, *yt = nullptr, *w = nullptr, *piece_buf = nullptr;
+  double* y_prev = nullptr;  // direct formulation: y of the previous outer iteration
   int32_t* slot = nullptr;
   float* perm = nullptr;
   double* permd = nullptr;  // class-ordered FP64 values (df64 evaluation)
@@ -227,7 +228,10 @@ int hessvec_tcx(manidsdp_ctx* c, int p, cudaStream_t s, const std::function<void
   if (mark) mark(1);
   launch_tcx_sddmm(N, p, c->Yxh, c->Yxl, c->Uxh, c->Uxl, ldp, c->slot, c->perm, c->Wfull, ldg,
                    c->tiles, c->ntiles, c->tc_err, s, c->tc_pairs);
-  launch_piece_sums(c->cm, c->perm, c->mult, reinterpret_cast<float*>(c->piece_buf), c->wf, s);
+  if (c->prm.direct)  // direct formulation: no class-mean term
+    MDS_CUDA(cudaMemsetAsync(c->wf, 0, size_t(c->m) * sizeof(float), s));
+  else
+    launch_piece_sums(c->cm, c->perm, c->mult, reinterpret_cast<float*>(c->piece_buf), c->wf, s);
   if (mark) mark(2);
   launch_tcx_split_matrix(N, c->Wfull, c->idx, c->wf, float(c->sigma), c->QWhi, c->QWlo, ldg, s);
   const int S = launch_tcx_gather(N, p, c->Ghi, c->Glo, c->QWhi, c->QWlo, ldg, c->UTh, c->UTl,
@@ -243,6 +247,10 @@ int hessvec_tcx(manidsdp_ctx* c, int p, cudaStream_t s, const std::function<void
 // w = A(Y Up' + Up Y') / mult in FP32 on the FMA engine (tiled SDDMM into the
 // class-ordered buffer, per-piece sums).
 void class_sums32(manidsdp_ctx* c, int p, cudaStream_t s) {
+  if (c->prm.direct) {  // direct formulation: no class-mean term
+    MDS_CUDA(cudaMemsetAsync(c->wf, 0, size_t(c->m) * sizeof(float), s));
+    return;
+  }
   float* pbf = reinterpret_cast<float*>(c->piece_buf);
   launch_sddmm_means(c->cm, c->N, p, c->Yf, c->Upf, c->slot, c->perm, c->mult, pbf, c->wf, s);
 }
@@ -310,12 +318,14 @@ void evaluate(manidsdp_ctx* c, const double* Y, int p, double* y, double* G, flo
     launch_split(size_t(c->N) * p, Y, c->Yh, c->Yl, c->s);
     launch_spass_df(c->cm, c->N, p, c->Yh, c->Yl, c->C, c->slot, c->Sup, c->permd, c->mult,
                     c->piece_buf, y, c->s);
-    launch_gpass_df(c->N, p, 0, c->Yh, c->Yl, c->idx, y, c->C, c->sigma, c->XD, G, Gh, Gl,
+    launch_gpass_df(c->N, p, 0, c->Yh, c->Yl, c->idx, c->prm.direct ? c->y_prev : y, c->C,
+                    c->sigma, c->XD, G, Gh, Gl,
                     c->part, c->out2, c->s, c->Sup);
   } else {
     launch_class_means<double>(c->cm, c->N, p, 0, Y, nullptr, c->C, c->mult, c->piece_buf, y,
                                c->s);
-    launch_gpass(c->N, p, 0, Y, c->idx, y, c->C, c->sigma, c->XD, G, Gf, c->part, c->out2, c->s);
+    launch_gpass(c->N, p, 0, Y, c->idx, c->prm.direct ? c->y_prev : y, c->C, c->sigma, c->XD, G,
+                 Gf, c->part, c->out2, c->s);
   }
   MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   tstop(c, &c->ms_eval);
@@ -359,8 +369,11 @@ void hessvec(manidsdp_ctx* c, const double* Y, const double* U, int p, double* H
   if (prec == MANIDSDP_PREC_FP64) {
     launch_hv_prep<double>(N, p, Y, U, c->Up, nullptr, nullptr, false, c->s);
     mark(1);
-    launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
-                               c->s);
+    if (c->prm.direct)  // direct formulation: no class-mean term (sigma I in place of sigma Q)
+      MDS_CUDA(cudaMemsetAsync(c->w, 0, size_t(c->m) * sizeof(double), c->s));
+    else
+      launch_class_means<double>(c->cm, N, p, 1, Y, c->Up, nullptr, c->mult, c->piece_buf, c->w,
+                                 c->s);
     mark(2);
     const int splits = launch_gemm_partials<double>(N, p, N, c->G, N, c->Up, p, c->idx, c->w,
                                                     -c->sigma, Y, c->gws, c->gws_bytes, c->s);
@@ -587,6 +600,7 @@ void default_params(manidsdp_params* p) {
   p->profile = 0;
   p->tcg_device = 1;
   p->tensor_cores = 0;
+  p->direct = 0;
 }
 
 // Ranges of the parameters (the switches are 0 or 1).
@@ -596,7 +610,7 @@ bool params_ok(const manidsdp_params& p) {
          p.delta_max >= 0 && p.lanczos_k >= 1 && p.max_outer >= 0 && p.max_rtr >= 0 &&
          p.max_tcg >= 1 && p.carry_halvings >= 0 &&
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
-         flag(p.tcg_device) && flag(p.warm_start) && flag(p.tensor_cores) &&
+         flag(p.tcg_device) && flag(p.warm_start) && flag(p.tensor_cores) && flag(p.direct) &&
          p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
          p.tol > 0.0 && p.tc_lowprec_eta >= 0.0;
 }
@@ -820,6 +834,8 @@ int manidsdp_setup(manidsdp_ctx** ctx_out, int32_t N, int64_t m, const int32_t* 
     c->yt = dalloc<double>(c, m);
     c->w = dalloc<double>(c, m);
     c->wf = dalloc<float>(c, m);
+    c->y_prev = dalloc<double>(c, m);
+    MDS_CUDA(cudaMemsetAsync(c->y_prev, 0, m * sizeof(double), c->s));
     c->piece_buf = dalloc<double>(c, pclass.size());
     c->slot = dalloc<int32_t>(c, NN);
     MDS_CUDA(cudaMemcpyAsync(c->slot, slot.data(), NN * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
@@ -896,7 +912,8 @@ int manidsdp_setup_ex(manidsdp_ctx** ctx_out, const manidsdp_problem* pr,
     default_params(&prm);
   if (!params_ok(prm)) return MANIDSDP_E_ARG;
   if (pr->is_complex) {
-    if (pr->N < 1 || 2 * int64_t(pr->N) > kMaxN || pr->q_re == nullptr) return MANIDSDP_E_ARG;
+    if (pr->N < 1 || 2 * int64_t(pr->N) > kMaxN || pr->q_re == nullptr || prm.direct)
+      return MANIDSDP_E_ARG;
     auto* c = new (std::nothrow) manidsdp_ctx();
     if (c == nullptr) return MANIDSDP_E_NOMEM;
     c->N = pr->N;
@@ -957,11 +974,22 @@ int manidsdp_set_params(manidsdp_ctx* c, const manidsdp_params* prm) {
   if (c == nullptr || prm == nullptr || !params_ok(*prm) || prm->p_max != c->prm.p_max ||
       prm->precision_mode != c->prm.precision_mode)
     return MANIDSDP_E_ARG;
-  const bool engine_changed = prm->tensor_cores != c->prm.tensor_cores;
+  const bool engine_changed =
+      prm->tensor_cores != c->prm.tensor_cores || prm->direct != c->prm.direct;
   c->prm = *prm;
   c->kmax = std::min(std::max(c->prm.lanczos_k, 1), std::min(c->kmax, c->N));
   if (engine_changed) drop_graphs(c);  // cached tCG graphs hold the old gather GEMM
   return MANIDSDP_OK;
+}
+
+int manidsdp_set_direct_y(manidsdp_ctx* c, const double* y) {
+  if (c == nullptr || c->cx != nullptr || y == nullptr) return MANIDSDP_E_ARG;
+  return guard([&]() -> int {
+    MDS_CUDA(cudaMemcpyAsync(c->y_prev, y, size_t(c->m) * sizeof(double), cudaMemcpyDefault, c->s));
+    c->eval_ok = false;
+    sync(c);
+    return MANIDSDP_OK;
+  });
 }
 
 int manidsdp_set_state(manidsdp_ctx* c, const double* Xt, double sigma) {
@@ -1343,6 +1371,15 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       c->resume_outer = 0;
       MDS_CUDA(cudaMemcpyAsync(c->tmp, Y0, size_t(N) * p * sizeof(double), cudaMemcpyDefault, c->s));
       launch_retract(N, p, c->tmp, c->tmp, 0.0, c->Y, c->s);
+      if (P.direct) {  // the direct formulation's first frozen y: y(S0 + C)
+        double f0, r20;
+        const bool mx = mixed(c);
+        evaluate(c, c->Y, p, c->y, mx ? nullptr : c->G, nullptr, &f0, &r20, mx ? c->Gh : nullptr,
+                 mx ? c->Gl : nullptr);
+        MDS_CUDA(cudaMemcpyAsync(c->y_prev, c->y, size_t(c->m) * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->s));
+        c->eval_ok = false;
+      }
     }
     bool have_U = resume && c->resume_have_U;
     int U_cols = have_U ? c->resume_U_cols : 0;
@@ -1400,6 +1437,9 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
         launch_gpass(N, p, 1, c->Y, c->idx, c->y, c->C, sigma, c->XD, nullptr, nullptr, c->part,
                      c->out2, c->s);
       }
+      if (P.direct)  // the next subproblem's frozen y (direct formulation's y-update)
+        MDS_CUDA(cudaMemcpyAsync(c->y_prev, c->y, size_t(c->m) * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->s));
       MDS_CUDA(cudaMemcpyAsync(c->hp, c->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
       sync(c);
       const double rnorm = std::sqrt(c->hp[0]);

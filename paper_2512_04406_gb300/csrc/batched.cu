@@ -143,7 +143,7 @@ bool batch_params_ok(const manidsdp_params& p) {
          p.max_outer >= 0 && p.max_rtr >= 0 && p.max_tcg >= 1 && p.carry_halvings >= 0 &&
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
          p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
-         p.tol > 0.0;
+         p.tol > 0.0 && p.direct == 0;
 }
 
 int catch_all(const std::function<int()>& f) {
