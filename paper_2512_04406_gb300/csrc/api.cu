@@ -1214,7 +1214,11 @@ manidsdp_ctx::Graph& tcg_graph_for(manidsdp_ctx* c, int p, int prec) {
   const int neb = tcg_epilogue_blocks(N);
   if (prec == MANIDSDP_PREC_FP64) {
     launch_tcg_prep<double>(N, p, c->tcgst, c->Y, c->r, c->delta, c->Up, nullptr, s);
-    launch_class_means<double>(c->cm, N, p, 1, c->Y, c->Up, nullptr, c->mult, c->piece_buf, c->w, s);
+    if (c->prm.direct)  // direct formulation: no class-mean term
+      MDS_CUDA(cudaMemsetAsync(c->w, 0, size_t(c->m) * sizeof(double), s));
+    else
+      launch_class_means<double>(c->cm, N, p, 1, c->Y, c->Up, nullptr, c->mult, c->piece_buf,
+                                 c->w, s);
     const int splits = launch_gemm_partials<double>(N, p, N, c->G, N, c->Up, p, c->idx, c->w,
                                                     -c->sigma, c->Y, c->gws, c->gws_bytes, s);
     launch_gram2<double>(N, p, c->Up, c->Y, c->Y, c->M1, c->gws2, c->gws2_bytes, s);

@@ -51,8 +51,9 @@ def test_direct_subproblem_eval_and_hessvec(prec, tc):
         mds.manidsdp_destroy(ctx)
 
 
-@pytest.mark.parametrize("q,seed", [(5, 0), (8, 2)])
-def test_direct_solve_reaches_the_projected_value(q, seed):
+@pytest.mark.parametrize("q,seed,prec,tc", [(5, 0, mds.PREC_FP64, 0), (8, 2, mds.PREC_FP64, 0),
+                                            (8, 2, mds.PREC_MIXED, 1), (10, 0, mds.PREC_MIXED, 1)])
+def test_direct_solve_reaches_the_projected_value(q, seed, prec, tc):
     torch_cuda()
     Q, c = bqp_instance(q, seed)
     N, m, idx = mds.manidsdp_bqp_index_map(q, 2)
@@ -61,6 +62,7 @@ def test_direct_solve_reaches_the_projected_value(q, seed):
     out = {}
     for name, dflag in (("projected", 0), ("direct", 1)):
         prm = mds.manidsdp_default_params()
+        prm.precision_mode, prm.tensor_cores = prec, tc
         prm.direct = dflag
         if dflag:
             prm.sigma0, prm.kappa1, prm.kappa2, prm.max_outer = 0.25, -1.0, 1e300, 1000
