@@ -381,6 +381,7 @@ def run_formulation_curve(mds, torch, qs, engine, stream):
             prm.direct = dflag
             if dflag:
                 prm.sigma0, prm.kappa1, prm.kappa2, prm.max_outer = 0.25, -1.0, 1e300, 1000
+                prm.sigma_stall = 0.0
             ctx = mds.manidsdp_setup(N, m, idx, b, params=prm, stream=stream.cuda_stream)
             solve_once(mds, torch, ctx, Y0, p0, stream)  # warm-up (graphs, allocations)
             rep, p, ms = solve_once(mds, torch, ctx, Y0, p0, stream)

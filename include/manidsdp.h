@@ -122,6 +122,13 @@ typedef struct {
                              place of sigma Q); the multiplier update is unchanged.  0
                              (default): the variable-projected (DSDP') of Algorithm 1.
                              manidsdp_solve only (not the batched or complex paths) */
+  double sigma_stall;     /* safeguard beside rule (5.1) (default 0.5; 0 = off, the rule as
+                             printed): after a subproblem solved to its tolerance in which
+                             neither branch of (5.1) fired, sigma <- min(gamma sigma,
+                             sigma_max) when ||R^{k+1}|| > sigma_stall ||R^k||
+                             (0 <= sigma_stall < 1).  The printed rule cannot raise sigma once
+                             eps_k tracks ||R||, so a sigma lowered during the capped early
+                             subproblems stays low and the ALM crawls */
 } manidsdp_params;
 
 /* Per-solve report (host struct filled by manidsdp_solve). */

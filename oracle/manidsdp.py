@@ -35,6 +35,12 @@ Readings where the paper is silent (each also listed in the design notes):
     (Solving every subproblem to eps_k, up to 200 RTR iterations, stalled on the
     q = 80 relaxation with p held at 256: RTR at its cap in every outer
     iteration.)
+  * Stall safeguard (sigma_stall = 0.5; 0 turns it off): after a subproblem
+    solved to eps_k in which neither branch of (5.1) fired, sigma doubles when the
+    scaled residual did not drop below sigma_stall times the previous one.  With
+    eps_k tracking ||R|| a solved subproblem leaves ||grad|| close to eps_k, so the
+    increase branch of (5.1) (kappa_2 = 10) cannot fire and a sigma lowered during
+    capped early subproblems stays low.
   * tCG also stops once ||r_j|| <= tcg_abs * eps_k (tcg_abs = 0.1): the RTR
     asks for ||grad|| <= eps_k, so resolving the model gradient further is wasted.
   * Use of the carried U (step 3, "supplied with"): if the exact curvature
@@ -70,7 +76,7 @@ DEFAULTS = dict(
     max_outer=300, max_rtr=15, max_tcg=60, tol=1e-8,
     tol_grad_min=1e-11, tol_grad_max=1e-2, tol_grad_factor=1.0, tcg_floor=1e-10, tcg_abs=0.1,
     rank_tol=1e-6, neg_tol=1e-10, carry_halvings=30, carry_t0=0.0, round_eta=1e-2,
-    lanczos_k=2000,
+    lanczos_k=2000, sigma_stall=0.5,
 )
 
 
@@ -252,10 +258,16 @@ def solve(prob, Y0, params=None, eig="dense", history=None, direct=False):
             p = Y.shape[1]
         # step 11: sigma rule, Eq. (5.1)
         lhs = float(np.linalg.norm(R)) / (1.0 + float(np.linalg.norm(b)))
+        lhs_prev = rscale
         rscale = lhs
         if lhs < prm["kappa1"] * gnorm:
             sigma = max(sigma / prm["gamma"], prm["sigma_min"])
         elif lhs > prm["kappa2"] * gnorm:
+            sigma = min(prm["gamma"] * sigma, prm["sigma_max"])
+        elif (prm["sigma_stall"] > 0 and lhs_prev is not None and gnorm <= tol_k
+              and lhs > prm["sigma_stall"] * lhs_prev):
+            # the stall safeguard (off by default): rule (5.1) cannot raise sigma once
+            # eps_k tracks ||R||
             sigma = min(prm["gamma"] * sigma, prm["sigma_max"])
         # steps 9 and 10 (second half): negative curvature -> rank augmentation
         thr = -prm["neg_tol"] * (1.0 + abs(lam_max))

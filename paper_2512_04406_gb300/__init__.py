@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
         (n, ctypes.c_int32) for n in (
             "p0", "p_min", "p_max", "delta_max", "max_outer", "max_rtr", "max_tcg",
             "carry_halvings", "lanczos_k", "precision_mode", "verbose", "profile", "tcg_device",
-            "warm_start", "tensor_cores", "direct")]
+            "warm_start", "tensor_cores", "direct")] + [("sigma_stall", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

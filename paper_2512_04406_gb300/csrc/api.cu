@@ -601,6 +601,7 @@ void default_params(manidsdp_params* p) {
   p->tcg_device = 1;
   p->tensor_cores = 0;
   p->direct = 0;
+  p->sigma_stall = 0.5;
 }
 
 // Ranges of the parameters (the switches are 0 or 1).
@@ -612,7 +613,7 @@ bool params_ok(const manidsdp_params& p) {
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
          flag(p.tcg_device) && flag(p.warm_start) && flag(p.tensor_cores) && flag(p.direct) &&
          p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
-         p.tol > 0.0 && p.tc_lowprec_eta >= 0.0;
+         p.tol > 0.0 && p.tc_lowprec_eta >= 0.0 && p.sigma_stall >= 0.0 && p.sigma_stall < 1.0;
 }
 
 struct NonFinite {};
@@ -1575,10 +1576,14 @@ extern "C" int manidsdp_solve(manidsdp_ctx* c, const double* Y0, int32_t p0, dou
       }
       // step 11: sigma rule (5.1)
       const double lhs = rnorm / (1.0 + c->normb);
+      const double lhs_prev = rscale;
       rscale = lhs;
       if (lhs < P.kappa1 * ro.gnorm)
         sigma = std::max(sigma / P.gamma, P.sigma_min);
       else if (lhs > P.kappa2 * ro.gnorm)
+        sigma = std::min(P.gamma * sigma, P.sigma_max);
+      else if (P.sigma_stall > 0.0 && lhs_prev > 0.0 && ro.gnorm <= tol_k &&
+               lhs > P.sigma_stall * lhs_prev)  // stalled primal residual (params.sigma_stall)
         sigma = std::min(P.gamma * sigma, P.sigma_max);
       // steps 9-10 (second half): negative curvature -> U = [0, V], Y = [Y, 0]
       const double thr = -P.neg_tol * (1.0 + std::fabs(lo.hi));

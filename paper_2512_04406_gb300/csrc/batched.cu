@@ -45,7 +45,7 @@ BParams to_bparams(const manidsdp_params& p) {
   b.kappa1 = p.kappa1; b.kappa2 = p.kappa2; b.tol = p.tol; b.tol_grad_min = p.tol_grad_min;
   b.tol_grad_max = p.tol_grad_max; b.tol_grad_factor = p.tol_grad_factor; b.rank_tol = p.rank_tol;
   b.neg_tol = p.neg_tol; b.tcg_floor = p.tcg_floor; b.tcg_abs = p.tcg_abs; b.carry_t0 = p.carry_t0;
-  b.round_eta = p.round_eta; b.p0 = p.p0; b.p_min = p.p_min; b.p_max = p.p_max;
+  b.round_eta = p.round_eta; b.sigma_stall = p.sigma_stall; b.p0 = p.p0; b.p_min = p.p_min; b.p_max = p.p_max;
   b.delta_max = p.delta_max; b.max_outer = p.max_outer; b.max_rtr = p.max_rtr;
   b.max_tcg = p.max_tcg; b.carry_halvings = p.carry_halvings;
   b.fp64 = p.precision_mode == MANIDSDP_PREC_FP64 ? 1 : 0;
@@ -143,7 +143,7 @@ bool batch_params_ok(const manidsdp_params& p) {
          p.max_outer >= 0 && p.max_rtr >= 0 && p.max_tcg >= 1 && p.carry_halvings >= 0 &&
          (p.precision_mode == MANIDSDP_PREC_FP64 || p.precision_mode == MANIDSDP_PREC_MIXED) &&
          p.sigma0 > 0.0 && p.sigma_min > 0.0 && p.sigma_max >= p.sigma_min && p.gamma > 1.0 &&
-         p.tol > 0.0 && p.direct == 0;
+         p.tol > 0.0 && p.direct == 0 && p.sigma_stall >= 0.0 && p.sigma_stall < 1.0;
 }
 
 int catch_all(const std::function<int()>& f) {

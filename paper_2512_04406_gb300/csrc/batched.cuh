@@ -32,7 +32,7 @@ struct BInst {
 struct BParams {
   double sigma0, sigma_min, sigma_max, gamma, kappa1, kappa2, tol;
   double tol_grad_min, tol_grad_max, tol_grad_factor, rank_tol, neg_tol, tcg_floor, tcg_abs;
-  double carry_t0, round_eta;
+  double carry_t0, round_eta, sigma_stall;
   int p0, p_min, p_max, delta_max, max_outer, max_rtr, max_tcg, carry_halvings;
   int fp64;     // 1: FP64 Hessian-vector products (MANIDSDP_PREC_FP64)
   int profile;  // 1: per-phase clock64 cycles into BOut::cycles

@@ -1035,11 +1035,14 @@ __device__ void bsolve(BCtx& c, const BParams& P, const double* Y0, BOut* out, d
     }
     // step 11: sigma rule (5.1)
     const double lhs = sqrt(r2) / (1.0 + normb);
+    const double lhs_prev = rscale;
     rscale = lhs;
     if (lhs < P.kappa1 * gnorm)
       sigma = fmax(sigma / P.gamma, P.sigma_min);
     else if (lhs > P.kappa2 * gnorm)
       sigma = fmin(P.gamma * sigma, P.sigma_max);
+    else if (P.sigma_stall > 0.0 && lhs_prev > 0.0 && gnorm <= tol_k && lhs > P.sigma_stall * lhs_prev)
+      sigma = fmin(P.gamma * sigma, P.sigma_max);  // stalled primal residual
     // steps 9-10: negative curvature -> Y = [Y, 0], U = [0, V]
     const int pc = c.p;
     const int delta = min(min(ce.nneg, P.delta_max), min(P.p_max, kBMaxP) - pc);

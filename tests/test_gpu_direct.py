@@ -71,6 +71,7 @@ def test_direct_solve_reaches_the_projected_value(q, seed, prec, tc):
         prm.direct = dflag
         if dflag:
             prm.sigma0, prm.kappa1, prm.kappa2, prm.max_outer = 0.25, -1.0, 1e300, 1000
+            prm.sigma_stall = 0.0
         ctx = mds.manidsdp_setup(N, m, idx, b, params=prm)
         try:
             out[name], _ = mds.manidsdp_solve(ctx, Y0, 2)
@@ -79,7 +80,8 @@ def test_direct_solve_reaches_the_projected_value(q, seed, prec, tc):
     ref_idx = moment.index_map(q)
     prob = om.make_problem(ref_idx, moment.multiplicities(ref_idx, m), moment.rhs(q, Q, c))
     ref = om.solve(prob, Y0, direct=True,
-                   params=dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, max_outer=1000))
+                   params=dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, sigma_stall=0.0,
+                               max_outer=1000))
     pr, dr = out["projected"], out["direct"]
     print(f"q={q}: projected {pr.outer} outer, direct {dr.outer} outer (oracle {ref['outer']})")
     assert pr.status == mds.OK and dr.status == mds.OK and dr.eta_max <= 1e-8
@@ -98,6 +100,7 @@ def test_direct_first_outer_iterations_follow_the_oracle():
     prm = mds.manidsdp_default_params()
     prm.direct = 1
     prm.sigma0, prm.kappa1, prm.kappa2, prm.max_outer = 0.25, -1.0, 1e300, k
+    prm.sigma_stall = 0.0
     ctx = mds.manidsdp_setup(N, m, idx, b, params=prm)
     try:
         rep, _ = mds.manidsdp_solve(ctx, Y0, 2)
@@ -107,7 +110,7 @@ def test_direct_first_outer_iterations_follow_the_oracle():
     prob = om.make_problem(ref_idx, moment.multiplicities(ref_idx, m), moment.rhs(q, Q, c))
     hist = []
     om.solve(prob, Y0, direct=True, history=hist,
-             params=dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, max_outer=k))
+             params=dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, sigma_stall=0.0, max_outer=k))
     h = hist[-1]
     print(f"after {k} outer iterations: eta_p {rep.eta_p:.6e} (oracle {h['eta_p']:.6e}), "
           f"value {rep.value:.10f} (oracle {h['dobj']:.10f})")

@@ -103,7 +103,7 @@ def test_direct_scheme_reaches_the_projected_value(q, seed):
     prob = om.make_problem(idx, moment.multiplicities(idx, len(b)), b)
     Y0 = gaussian_factor(idx.shape[0], 2, seed)
     ref = om.solve(prob, Y0)
-    fixed = dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, max_outer=1000)
+    fixed = dict(sigma0=0.25, kappa1=-1.0, kappa2=1e300, sigma_stall=0.0, max_outer=1000)
     res = om.solve(prob, Y0, direct=True, params=fixed)
     assert max(ref["eta"]) <= 1e-8 and max(res["eta"]) <= 1e-8
     assert abs(res["value"] - ref["value"]) <= 1e-8 * abs(ref["value"])
