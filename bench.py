@@ -63,8 +63,8 @@ UNIT = "s/solve"
 # tensor-core engine (GB300 run of this bench), used to scale the oracle's
 # sampled timings to one solve when no GPU run precedes them (the reference arm).
 # The GPU arm uses the counts of its own timed solves.
-DEFAULT_COUNTS = dict(hessvecs=25891, evals=948, grads=591, lanczos_matvecs=20900, p=339,
-                      outer=43)
+DEFAULT_COUNTS = dict(hessvecs=20885, evals=820, lanczos_matvecs=21230, p=298,
+                      outer=36)
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one
 # Hess-vec) from one ncu capture at q = 80, per p; "current" is False when the
