@@ -66,3 +66,45 @@ def test_q20_dense_bqp_brute_force_2_pow_20():
     fmin, xmin = brute.bqp_min(Q, c)
     assert res["value"] <= fmin + 1e-8 * (1 + abs(fmin))
     assert res["value"] == pytest.approx(fmin, rel=1e-9)
+
+
+def _problem(q, seed):
+    Q, c = bqp_instance(q, seed)
+    idx = moment.index_map(q)
+    b = moment.rhs(q, Q, c)
+    return manidsdp.make_problem(idx, moment.multiplicities(idx, len(b)), b), b
+
+
+@pytest.mark.parametrize("q,seed", [(6, 0), (8, 1), (10, 2)])
+def test_sigma_sequence_follows_rule_5_1_and_the_stall_safeguard(q, seed):
+    """The penalty sequence of a solve obeys Eq. (5.1) with kappa_1 = 0.1, kappa_2 = 10,
+    gamma = 2 and, when neither branch fires, the stall safeguard: sigma doubles after
+    a subproblem solved to eps_k = clamp(||R_prev|| / (1 + ||b||), 1e-11, 1e-2) whose
+    scaled residual exceeds half the previous one.  Reconstructed from the history
+    (eta_p = ||R|| with C = 0, the RTR's final gradient norm), for the safeguard on
+    and off; both settings reach the same value."""
+    prob, b = _problem(q, seed)
+    Y0 = gaussian_factor(prob["N"], 2, seed)
+    nb = 1.0 + float(np.linalg.norm(b))
+    values = []
+    for stall in (0.0, 0.5):
+        hist = []
+        res = manidsdp.solve(prob, Y0, dict(sigma_stall=stall), history=hist)
+        assert max(res["eta"]) <= 1e-8
+        values.append(res["value"])
+        steps = [h for h in hist if not h.get("rounded")]
+        prev = None
+        for h, nxt in zip(steps, steps[1:]):
+            lhs, g, s = h["eta_p"] / nb, h["gnorm"], h["sigma"]
+            tol_k = 1e-2 if prev is None else max(1e-11, min(1e-2, prev))
+            if lhs < 0.1 * g:
+                want = max(s / 2.0, 1e-3)
+            elif lhs > 10.0 * g:
+                want = min(2.0 * s, 1e6)
+            elif stall > 0 and prev is not None and g <= tol_k and lhs > stall * prev:
+                want = min(2.0 * s, 1e6)
+            else:
+                want = s
+            assert nxt["sigma"] == want, (h["k"], s, nxt["sigma"], want)
+            prev = lhs
+    assert abs(values[0] - values[1]) <= 1e-9 * abs(values[0])
