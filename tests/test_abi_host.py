@@ -90,7 +90,9 @@ def test_setup_rejects_bad_index_maps_before_touching_the_gpu():
 
 @pytest.mark.parametrize("field,value", [("tensor_cores", 2), ("precision_mode", 5),
                                          ("tcg_device", -1), ("warm_start", 3), ("gamma", 1.0),
-                                         ("p_max", 513), ("max_tcg", 0), ("sigma0", 0.0)])
+                                         ("p_max", 513), ("max_tcg", 0), ("sigma0", 0.0),
+                                         ("direct", 2), ("sigma_stall", 1.0),
+                                         ("sigma_stall", -0.5)])
 def test_setup_rejects_out_of_range_params_before_touching_the_gpu(field, value):
     N, m, idx = mds.manidsdp_bqp_index_map(3, 2)
     prm = mds.manidsdp_default_params()
@@ -182,7 +184,8 @@ def test_batch_setup_rejects_bad_instances_before_touching_the_gpu():
     with pytest.raises(mds.ManidsdpError) as e:
         mds.manidsdp_batch_setup([N3], [m3], [idx3], [np.zeros(m3)])
     assert e.value.status == mds.E_ARG
-    for field, value in (("p_max", 33), ("p0", 0), ("precision_mode", 4), ("gamma", 0.5)):
+    for field, value in (("p_max", 33), ("p0", 0), ("precision_mode", 4), ("gamma", 0.5),
+                         ("direct", 1), ("sigma_stall", 1.5)):
         prm = mds.manidsdp_default_params()
         prm.p_max = 32
         setattr(prm, field, value)
@@ -195,3 +198,14 @@ def test_batch_setup_rejects_bad_instances_before_touching_the_gpu():
     with pytest.raises(mds.ManidsdpError) as e:
         mds.manidsdp_batch_setup([N1], [m1], [idx1], [b_nan])
     assert e.value.status == mds.E_NONFINITE
+
+
+def test_complex_setup_rejects_the_direct_formulation_before_touching_the_gpu():
+    """The first-order complex relaxation has no frozen-y formulation (every entry is
+    its own class, R = 0): setup_ex refuses params.direct = 1 for it."""
+    prm = mds.manidsdp_default_params()
+    prm.direct = 1
+    Q = np.eye(4, dtype=complex)
+    with pytest.raises(mds.ManidsdpError) as e:
+        mds.manidsdp_setup_complex(Q, prm)
+    assert e.value.status == mds.E_ARG
