@@ -1,7 +1,7 @@
 """Host logic of bench.py's multi-GPU mode (replicas: one solve per rank, no
 collective on the data path) on CPU: two gloo ranks reduce their timings the
 way the GPU ranks do (max of the timed-region lengths, sum of the completed
-outer iterations), and the reference arm prints from rank 0 only."""
+steps, one full solve each), and the reference arm prints from rank 0 only."""
 import os
 import socket
 import subprocess
