@@ -105,14 +105,16 @@ typedef struct {
                              negative-curvature direction left by the previous solve
                              (Y0/p0 ignored; a fresh start when no solve ran yet);
                              0 (default): start from Y0 with Xt = 0, sigma0 */
-  int32_t tensor_cores;   /* mixed form only: 1 runs the gather GEMM of the FP32
-                             Hessian-vector product on the tensor cores
-                             (tcgen05 kind::tf32, each operand split into two TF32
-                             halves, four products per step, FP32 accumulation in
-                             chains of at most 640 terms): Hess-vec error 0.5-2e-5
-                             relative at N = 3241-7261 against 2-5e-6 for the FP32
-                             FMA kernel; same speed at small p, faster at p <= 80
-                             for N ~ 3000.  0 (default): FP32 FMA kernel */
+  int32_t tensor_cores;   /* mixed form only: 1 runs the two dense contractions of the
+                             FP32 Hessian-vector product (the SDDMM W = Y U' + U Y' and
+                             the gather GEMM [G | sigma Q(W)] [U ; Y]) on the tensor
+                             cores: TMA-staged operands, tcgen05 kind::tf32 with each
+                             operand split into a TF32 pair and three products per K
+                             step, FP32 accumulation in chains of at most 640 terms.
+                             Hess-vec error within 5e-5 relative (measured 1-3e-5 at
+                             N = 3241-7261); about 2x the FP32 FMA kernels at p ~ 300
+                             (0.47 vs 0.99 ms at N = 3241, p = 330).  0 (default): FP32
+                             FMA kernels */
   int32_t direct;         /* 1: the direct two-block ADMM on (DSDP) itself (Section 3, the
                              comparison with the direct subproblem, Eq.
                              (direct-ALM-subproblem)): each subproblem keeps y frozen at the
